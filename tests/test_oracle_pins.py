@@ -1,0 +1,341 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the values
+the paper prints (tests/golden), closed forms of the lattice, invariants of
+the update (rest state, mass, momentum), analytic flows (Taylor-Green decay,
+Poiseuille parabola) and independent brute-force constructions.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2108_13241_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _walls(moving_north=(0.0, 0.0)):
+    return [(0.0, 0.0), (0.0, 0.0), (0.0, 0.0), moving_north]
+
+
+# ---------------------------------------------------------------- lattice
+
+def test_lattice_matches_paper_golden(orc):
+    """c_i, w_i and the numbering as printed in Sec. 2.2 (Fig. D2Q9, Eq. f^eq)."""
+    cx, cy, w, opp = orc.lattice()
+    rows = np.loadtxt(os.path.join(GOLDEN, "lattice_d2q9.txt"))
+    assert np.array_equal(cx, rows[:, 1].astype(int))
+    assert np.array_equal(cy, rows[:, 2].astype(int))
+    assert np.allclose(w, rows[:, 3] / rows[:, 4], rtol=0, atol=1e-17)
+    assert np.array_equal(cx[opp], -cx) and np.array_equal(cy[opp], -cy)
+
+
+def test_lattice_isotropy_closed_forms(orc):
+    """sum w = 1, sum w c = 0, sum w c_a c_b = delta/3, 4th moment = (dd+dd+dd)/9."""
+    cx, cy, w, _ = orc.lattice()
+    c = np.stack([cx, cy]).astype(float)
+    assert abs(w.sum() - 1) < 1e-15
+    assert np.abs(c @ w).max() < 1e-16
+    assert np.allclose(np.einsum("i,ai,bi->ab", w, c, c), np.eye(2) / 3, atol=1e-16)
+    d = np.eye(2)
+    t4 = np.einsum("i,ai,bi,ci,di->abcd", w, c, c, c, c)
+    iso = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+           + np.einsum("ad,bc->abcd", d, d)) / 9
+    assert np.allclose(t4, iso, atol=1e-16)
+
+
+def test_equilibrium_moments_closed_form(orc):
+    """f^eq of Eq. (f^eq) has density rho and momentum rho u exactly."""
+    s = orc.Setup(nx=8, ny=6, tau=0.7)
+    mask, _ = orc.link_mask(s)
+    rho = 1 + 0.1 * inputs.random_field((6, 8), 1)
+    u = 0.1 * inputs.random_field((2, 6, 8), 2)
+    A = orc.init_equilibrium(s, mask, rho, u)
+    cx, cy, _, _ = orc.lattice()
+    assert np.allclose(A.sum(0), rho, rtol=1e-15, atol=0)
+    assert np.allclose(np.tensordot(cx, A, 1), rho * u[0], atol=1e-16)
+    assert np.allclose(np.tensordot(cy, A, 1), rho * u[1], atol=1e-16)
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("px,py", [(1, 1), (1, 0), (0, 1), (0, 0)])
+def test_rest_state_invariance(orc, px, py):
+    """rho = 1, u = 0, F = 0 is a fixed point for any mask and any sides."""
+    nx, ny = 24, 20
+    s = orc.Setup(nx=nx, ny=ny, tau=0.9, periodic_x=bool(px), periodic_y=bool(py))
+    solid = inputs.random_solid(nx, ny, 0.25, seed=11 + 2 * px + py)
+    mask, _ = orc.link_mask(s, solid)
+    A0 = orc.init_equilibrium(s, mask)
+    A = orc.run(s, mask, A0, 50)
+    assert np.abs(A - A0).max() <= 50 * 2 * np.spacing(4 / 9)
+
+
+@pytest.mark.parametrize("case", ["cavity", "porous_force", "periodic_force"])
+def test_mass_conservation(orc, case):
+    """sum over fluid nodes of sum_i A_i is invariant to round-off (1000 steps)."""
+    nx, ny = 32, 32
+    if case == "cavity":
+        s = orc.Setup(nx=nx, ny=ny, tau=0.6, periodic_x=False, periodic_y=False,
+                      wall_u=_walls((0.1, 0.0)))
+        solid = None
+    elif case == "porous_force":
+        s = orc.Setup(nx=nx, ny=ny, tau=0.8, periodic_x=True, periodic_y=False,
+                      wall_u=[(0, 0), (0, 0), (0.02, 0.0), (-0.03, 0.0)], force=(1e-4, 2e-5))
+        solid = inputs.random_solid(nx, ny, 0.2, seed=5)
+    else:
+        s = orc.Setup(nx=nx, ny=ny, tau=0.8, force=(1e-4, -3e-5))
+        solid = inputs.random_solid(nx, ny, 0.1, seed=6)
+    mask, nf = orc.link_mask(s, solid)
+    rho = 1 + 0.01 * inputs.random_field((ny, nx), 3)
+    u = 0.02 * inputs.random_field((2, ny, nx), 4)
+    A0 = orc.init_equilibrium(s, mask, rho, u)
+    A = orc.run(s, mask, A0, 1000)
+    m0, m1 = orc.mass(A0, mask), orc.mass(A, mask)
+    assert abs(m1 - m0) / m0 <= 1e-13
+
+
+def test_momentum_grows_by_force_each_step(orc):
+    """Periodic, all fluid: total momentum changes by exactly N F per step
+    (streaming permutes, BGK keeps rho u, the Guo source adds F)."""
+    nx, ny = 16, 12
+    F = (1e-4, -2e-4)
+    s = orc.Setup(nx=nx, ny=ny, tau=0.75, force=F)
+    mask, nf = orc.link_mask(s)
+    rho = 1 + 0.01 * inputs.random_field((ny, nx), 8)
+    u = 0.05 * inputs.random_field((2, ny, nx), 9)
+    A = orc.init_equilibrium(s, mask, rho, u)
+    px, py = orc.momentum(A, mask)
+    for _ in range(20):
+        A = orc.step(s, mask, A)
+        qx, qy = orc.momentum(A, mask)
+        assert abs(qx - px - nf * F[0]) < 1e-13
+        assert abs(qy - py - nf * F[1]) < 1e-13
+        px, py = qx, qy
+
+
+def test_per_node_force_equals_uniform(orc):
+    """A per-node force field equal everywhere to F gives the uniform-F result."""
+    nx, ny = 16, 16
+    s = orc.Setup(nx=nx, ny=ny, tau=0.8, periodic_y=False, force=(3e-5, 1e-5))
+    mask, _ = orc.link_mask(s, inputs.random_solid(nx, ny, 0.15, 21))
+    A0 = orc.init_equilibrium(s, mask)
+    field = np.zeros((2, ny, nx))
+    field[0], field[1] = 3e-5, 1e-5
+    a = orc.run(s, mask, A0, 30)
+    s0 = orc.Setup(nx=nx, ny=ny, tau=0.8, periodic_y=False)
+    b = orc.run(s0, mask, A0, 30, force=field)
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- flows
+
+def _ke(orc, s, mask, A):
+    rho, u = orc.macros(s, mask, A)
+    return orc.loss_ke(rho, u, mask)
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_taylor_green_decay_rate(orc, n):
+    """Kinetic energy decays as exp(-4 nu k^2 t), nu = (tau - 1/2)/3 (Eq. omega)."""
+    tau, U = 0.8, 0.01
+    s = orc.Setup(nx=n, ny=n, tau=tau)
+    mask, _ = orc.link_mask(s)
+    rho, u = inputs.taylor_green(n, n, U)
+    A = orc.init_equilibrium(s, mask, rho, u)
+    A = orc.run(s, mask, A, 100)
+    ts, ks = [], []
+    steps = int(2000 * (n / 64) ** 2)
+    chunk = steps // 10
+    for k in range(11):
+        ts.append(k * chunk)
+        ks.append(_ke(orc, s, mask, A))
+        A = orc.run(s, mask, A, chunk)
+    rate = -np.polyfit(ts, np.log(ks), 1)[0]
+    nu = (tau - 0.5) / 3
+    expect = 4 * nu * (2 * math.pi / n) ** 2
+    err = abs(rate / expect - 1)
+    assert err < 0.01, err
+    # store for the convergence check
+    test_taylor_green_decay_rate.errs = getattr(test_taylor_green_decay_rate, "errs", {})
+    test_taylor_green_decay_rate.errs[n] = err
+
+
+def test_taylor_green_error_shrinks_with_resolution(orc):
+    errs = getattr(test_taylor_green_decay_rate, "errs", None)
+    if not errs or len(errs) < 2:
+        pytest.skip("decay-rate tests did not run")
+    assert errs[64] < errs[32] / 2.5
+
+
+def _poiseuille(orc, tau, ny=32, u_max=0.01):
+    nx = 4
+    # slowest mode decays as exp(-pi^2 nu t / ny^2): run ~40 of its time constants
+    steps = max(30000, int(4 * ny * ny / ((tau - 0.5) / 3)))
+    fx, rho, u = inputs.poiseuille(nx, ny, tau, u_max)
+    s = orc.Setup(nx=nx, ny=ny, tau=tau, periodic_x=True, periodic_y=False, force=(fx, 0.0))
+    mask, _ = orc.link_mask(s)
+    A = orc.init_equilibrium(s, mask, rho, u)
+    A = orc.run(s, mask, A, steps)
+    r, uu = orc.macros(s, mask, A)
+    return fx, r, uu
+
+
+def test_poiseuille_magic_tau_exact_parabola(orc):
+    """Half-way bounce-back + Guo force at tau = 1/2 + sqrt(3/16): the steady
+    profile is exactly u(y) = F/(2 nu) (y + 1/2)(ny - 1/2 - y) (walls half a
+    spacing outside the first and last rows; channel parabola, Sec. 4.1.2)."""
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    ny = 32
+    fx, r, u = _poiseuille(orc, tau, ny=ny)
+    nu = (tau - 0.5) / 3
+    y = np.arange(ny)
+    exact = fx / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    got = u[0][:, 0]
+    assert np.abs(got - exact).max() <= 1e-8 * exact.max()
+    assert np.abs(u[0] - u[0][:, :1]).max() < 1e-15  # uniform along x
+    assert np.abs(u[1]).max() < 1e-11 * exact.max()
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.2])
+def test_poiseuille_parabola_and_curvature(orc, tau):
+    """Any tau: the profile is exactly quadratic with curvature -F/(rho0 nu)."""
+    ny = 32
+    fx, r, u = _poiseuille(orc, tau, ny=ny)
+    nu = (tau - 0.5) / 3
+    y = np.arange(ny, dtype=float)
+    prof = u[0][:, 0]
+    c = np.polyfit(y, prof, 2)
+    resid = np.abs(np.polyval(c, y) - prof).max()
+    assert resid <= 1e-10 * prof.max()
+    assert abs(2 * c[0] / (-fx / nu) - 1) <= 1e-8
+    assert np.abs(r - 1).max() < 1e-10  # round-off over ~1e5 steps
+
+
+def test_cavity_lid_drags_top_row(orc):
+    """Moving north wall: u_x > 0 in the top row after a while (mass is pinned above)."""
+    n = 32
+    s = orc.Setup(nx=n, ny=n, tau=0.6, periodic_x=False, periodic_y=False,
+                  wall_u=_walls((0.1, 0.0)))
+    mask, _ = orc.link_mask(s)
+    A = orc.run(s, mask, orc.init_equilibrium(s, mask), 200)
+    _, u = orc.macros(s, mask, A)
+    assert (u[0][-1] > 0).all()
+    assert u[0][-1].max() < 0.1
+
+
+# ---------------------------------------------------------------- macros
+
+def test_macros_rest_and_uniform_flow(orc):
+    """Rest state gives u = 0, rho = 1; a uniform u0 on a periodic all-fluid
+    grid is returned exactly (gathering f^eq(u0) returns f^eq(u0))."""
+    s = orc.Setup(nx=12, ny=8, tau=0.7)
+    mask, _ = orc.link_mask(s)
+    A = orc.init_equilibrium(s, mask)
+    rho, u = orc.macros(s, mask, A)
+    assert np.abs(rho - 1).max() < 1e-15 and np.abs(u).max() == 0
+    u0 = np.zeros((2, 8, 12))
+    u0[0], u0[1] = 0.037, -0.021
+    A = orc.init_equilibrium(s, mask, None, u0)
+    rho, u = orc.macros(s, mask, A)
+    assert np.abs(u - u0).max() < 1e-16
+    assert np.abs(rho - 1).max() < 1e-15
+
+
+# ---------------------------------------------------------------- geometry tables
+
+def _mask_bruteforce(solid, px, py):
+    """Link mask by padding and shifting whole arrays (numpy), not per node."""
+    cx = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    cy = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    ny, nx = solid.shape
+    # pad: periodic axes wrap, wall axes with a ring marked 1 (outside)
+    p = np.pad(solid.astype(np.int64), ((1, 1), (1, 1)), mode="constant", constant_values=1)
+    p[1:-1, 1:-1] = solid
+    if px:
+        p[:, 0], p[:, -1] = p[:, -2], p[:, 1]
+    if py:
+        p[0, :], p[-1, :] = p[-2, :], p[1, :]
+    if px and not py:
+        p[0, :], p[-1, :] = 1, 1
+    if py and not px:
+        p[:, 0], p[:, -1] = 1, 1
+    mask = np.zeros((ny, nx), np.int64)
+    for i in range(1, 9):
+        src = p[1 - cy[i]:1 - cy[i] + ny, 1 - cx[i]:1 - cx[i] + nx]
+        mask |= (src != 0).astype(np.int64) << (i - 1)
+    mask[solid != 0] = 0xFF
+    return mask.astype(np.uint8)
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (16, 16), (48, 32), (33, 17)])
+@pytest.mark.parametrize("px,py", [(1, 1), (1, 0), (0, 1), (0, 0)])
+def test_link_mask_bruteforce(orc, shape, px, py):
+    ny, nx = shape
+    solid = inputs.random_solid(nx, ny, 0.3, seed=nx * 100 + ny + 7 * px + 3 * py)
+    s = orc.Setup(nx=nx, ny=ny, tau=0.8, periodic_x=bool(px), periodic_y=bool(py))
+    mask, nf = orc.link_mask(s, solid)
+    assert np.array_equal(mask, _mask_bruteforce(solid, px, py))
+    assert nf == int((mask != 0xFF).sum())
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (48, 48), (48, 32), (40, 24)])
+@pytest.mark.parametrize("px,py", [(1, 1), (1, 0), (0, 1), (0, 0)])
+def test_tile_map_invariants(orc, shape, px, py):
+    """The tile table is fixed by its invariants: kept <=> holds a fluid node,
+    ids 0..n-1 in row-major order, nbr[t][0] = t, nbr[t][i] is the tile at
+    offset c_i (wrapped on periodic axes, -1 beyond walls or when absent)."""
+    ny, nx = shape
+    if (px and nx % 16) or (py and ny % 16):
+        pytest.skip("periodic axes must be multiples of 16")
+    cx = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    cy = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    for frac, seed in [(0.0, 1), (0.6, 2), (0.97, 3), (1.0, 4)]:
+        solid = inputs.random_solid(nx, ny, frac, seed=seed + nx + ny)
+        # carve out whole empty tiles too
+        solid[:16, :16] = 1
+        s = orc.Setup(nx=nx, ny=ny, tau=0.8, periodic_x=bool(px), periodic_y=bool(py))
+        mask, _ = orc.link_mask(s, solid)
+        tid, nbr = orc.tile_map(s, mask)
+        nty, ntx = tid.shape
+        kept = []
+        for ty in range(nty):
+            for tx in range(ntx):
+                blk = mask[16 * ty:16 * ty + 16, 16 * tx:16 * tx + 16]
+                has = bool((blk != 0xFF).any())
+                assert (tid[ty, tx] >= 0) == has
+                if has:
+                    kept.append((ty, tx))
+        assert [tid[ty, tx] for ty, tx in kept] == list(range(len(kept)))
+        assert nbr.shape == (len(kept), 9)
+        for t, (ty, tx) in enumerate(kept):
+            assert nbr[t, 0] == t
+            for i in range(1, 9):
+                ux, uy = tx + cx[i], ty + cy[i]
+                out = False
+                if not 0 <= ux < ntx:
+                    out |= not px
+                    ux %= ntx
+                if not 0 <= uy < nty:
+                    out |= not py
+                    uy %= nty
+                want = -1 if out else int(tid[uy, ux])
+                assert nbr[t, i] == want
+        # symmetry: j = nbr[t][i] >= 0 implies nbr[j][opp i] = t
+        opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+        for t in range(len(kept)):
+            for i in range(9):
+                j = nbr[t, i]
+                if j >= 0:
+                    assert nbr[j, opp[i]] == t
+
+
+def test_isolated_fluid_node_counts_as_solid(orc):
+    """A fluid node whose 8 links all bounce gets the solid mask value."""
+    solid = np.ones((8, 16), np.uint8)
+    solid[4, 5] = 0
+    s = orc.Setup(nx=16, ny=8, tau=0.8)
+    mask, nf = orc.link_mask(s, solid)
+    assert nf == 0 and mask[4, 5] == 0xFF
