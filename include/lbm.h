@@ -1,0 +1,207 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D2Q9 lattice-Boltzmann library.
+ *
+ * The library implements the fused pull stream-and-collide update of
+ * Tomczak, "Data-Oriented Language Implementation of Lattice-Boltzmann Method
+ * for Dense and Sparse Geometries" (arXiv 2108.13241), Algorithm 1, with the
+ * BGK operator (Eq. Omega^BGK, Eq. omega, Eq. f^eq), the moments of
+ * Eq. (rho, v), half-way bounce-back walls and obstacles (Sec. 3, boundary
+ * paragraph), dense and 16x16-tiled sparse storage (Sec. 4.2.1, "tile" and
+ * "pointer tile" layouts), plus a Guo body force, an in-place AA pattern,
+ * FP64 / FP32 / FP16-shifted storage and a hand-written adjoint.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Lattice (Sec. 2.2, Fig. D2Q9): i = 0 rest, 1 (+1,0), 2 (0,+1), 3 (-1,0),
+ *  4 (0,-1), 5 (+1,+1), 6 (-1,+1), 7 (-1,-1), 8 (+1,-1).
+ *  Node (x, y) has index n = y*nx + x (x fastest).  Canonical device arrays:
+ *    distributions  f[i][ny][nx]  -- the post-collision state A_t, i.e. the
+ *                                    array the next step gathers
+ *                                    f'_i(x) = A_i(x - c_i) from;
+ *    vector fields  v[2][ny][nx]  (x component first);
+ *    scalar fields  s[ny][nx].
+ *  "Compute type" = double for LBM_F64, float for LBM_F32 and LBM_F16S; every
+ *  canonical device array passed to or from the library is in compute type.
+ *  Device pointers must be 16-byte aligned (torch allocations are).
+ *  Ownership: all device memory belongs to the caller.  lbm_create carves
+ *  its lattices and tables out of the caller's workspace; the context owns
+ *  host memory only.  Caller buffers must outlive the calls that use them
+ *  (the force field: until it is replaced or the context destroyed).
+ *  Streams: every call is asynchronous on params.stream unless it says it
+ *  synchronises.  Errors: every call returns a status and never aborts; a
+ *  CUDA launch or runtime error is also kept in the context ("sticky") and
+ *  returned by every later call; lbm_last_error gives the message.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID = 1,      /* bad argument or geometry                    */
+    LBM_ERR_CUDA = 2,         /* CUDA runtime error (sticky)                 */
+    LBM_ERR_OOM = 3,          /* workspace smaller than lbm_workspace_bytes  */
+    LBM_ERR_DIVERGED = 4,     /* a reduction met NaN/Inf                     */
+    LBM_ERR_TIMEOUT = 5,      /* reserved: no call here waits on the device  */
+    LBM_ERR_UNSUPPORTED = 6   /* valid request this build does not serve     */
+} lbm_status;
+
+/* Storage of the distributions.  Every mode stores f_i - w_i ("shifted");
+ * LBM_F16S rounds it to binary16 (round-to-nearest-even) and computes in
+ * FP32, LBM_F32 stores and computes FP32, LBM_F64 stores and computes FP64. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 } lbm_precision;
+
+/* LBM_DENSE: f[i][ny][nx].  LBM_SPARSE_TILE16: only 16x16 tiles that hold a
+ * fluid node are stored, f[tile][i][16][16], with a 9-entry neighbour-tile
+ * table (the paper's "pointer tile" layout without pointers). */
+typedef enum { LBM_DENSE = 0, LBM_SPARSE_TILE16 = 1 } lbm_layout;
+
+/* LBM_TWO_LATTICE: read A, write B, swap (Algorithm 1).  LBM_AA: one lattice
+ * updated in place, alternating a local step and a gather/scatter step (the
+ * single-copy scheme the paper cites in Sec. 3). */
+typedef enum { LBM_TWO_LATTICE = 0, LBM_AA = 1 } lbm_pattern;
+
+/* A domain side.  periodic != 0: the axis wraps (both sides of an axis must
+ * agree).  periodic == 0: half-way bounce-back wall half a spacing outside
+ * the outermost nodes, moving at (ux, uy); a link that crosses it gets the
+ * term 6 w_i rho_0 (c_i . u_w), rho_0 = 1.  A link that leaves the domain
+ * across two sides is decided by the south/north side first. */
+typedef struct {
+    int periodic;
+    double ux, uy;
+} lbm_side;
+
+typedef struct {
+    int nx, ny;               /* nx % 16 == 0; LBM_SPARSE_TILE16 with a
+                                 periodic y axis also needs ny % 16 == 0   */
+    const uint8_t *solid;     /* HOST [ny][nx], nonzero = solid; NULL = all
+                                 fluid; read during lbm_workspace_bytes and
+                                 lbm_create only                           */
+    double tau;               /* BGK relaxation time > 0.5; omega = 1/tau,
+                                 nu = (tau - 1/2)/3 (Eq. omega)            */
+    double fx, fy;            /* uniform body-force density (Guo forcing)  */
+    lbm_side west, east, south, north;
+    lbm_precision precision;
+    lbm_layout layout;
+    lbm_pattern pattern;
+    void *stream;             /* cudaStream_t, NULL = legacy default stream */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Bytes of device workspace lbm_create needs for these parameters.  Host
+ * only; builds the link mask and, for the sparse layout, the tile map. */
+lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes);
+
+/* Validates p, builds the per-node link mask (bit i-1 set iff link i pulls
+ * from a solid node or across a wall; 0xFF marks a node that is solid or has
+ * no link to any other node, Sec. 3 "bitmask containing information about
+ * which neighbour nodes are present") and, for the sparse layout, the tile
+ * map; copies them into d_workspace (>= lbm_workspace_bytes, 256-byte
+ * aligned) and initialises the lattice to rest (rho = 1, u = 0) (Algorithm 1,
+ * initialisation).  Synchronises the stream.  *out is NULL on error. */
+lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_ctx **out);
+
+/* Frees the host context.  The workspace stays the caller's. */
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Per-node body force F[2][ny][nx] (compute type), used by every later step,
+ * macros and adjoint instead of (fx, fy); NULL returns to the uniform force.
+ * The pointer is kept, not copied. */
+lbm_status lbm_set_force(lbm_ctx *ctx, const void *d_force);
+
+/* Algorithm 1, initialisation: A_i = f^eq_i(rho, u) (Eq. f^eq) at fluid
+ * nodes.  d_rho [ny][nx] and d_u [2][ny][nx] in compute type; NULL means
+ * rho = 1 / u = 0.  Resets the step counter and the AA phase. */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *d_rho, const void *d_u);
+
+/* n time steps of Algorithm 1 (n >= 0): per fluid node, pull gather with
+ * bounce-back, moments (Eq. rho, v, u shifted by F/2), f^eq (Eq. f^eq), BGK
+ * relaxation (Eq. LBM, Eq. Omega^BGK) plus the Guo source
+ * (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F, aligned store. */
+lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Density and velocity of the current state (Eq. rho, v on the gathered f'
+ * of the next step, u = (m + F/2)/rho).  d_rho [ny][nx], d_u [2][ny][nx]
+ * (compute type); either may be NULL.  Solid nodes give rho = 1, u = 0. */
+lbm_status lbm_macros(lbm_ctx *ctx, void *d_rho, void *d_u);
+
+/* Canonical state A_t out / in: d_f [9][ny][nx] compute type.  Solid nodes
+ * read as w_i and are ignored on input.  lbm_set_f resets the AA phase. */
+lbm_status lbm_get_f(lbm_ctx *ctx, void *d_f);
+lbm_status lbm_set_f(lbm_ctx *ctx, const void *d_f);
+
+/* FP64 reductions over fluid nodes of the canonical state: mass
+ * sum_i A_i and momentum sum_i c_i A_i.  Deterministic (fixed-order tree,
+ * no atomics).  Synchronises; LBM_ERR_DIVERGED on NaN/Inf.  Either output
+ * pointer may be NULL. */
+lbm_status lbm_reduce(lbm_ctx *ctx, double *h_mass, double h_mom[2]);
+
+/* FP64 loss of the current state over fluid nodes, Nf = fluid-node count:
+ * kind 0: (1/Nf) sum |u - u*|^2 with d_u_target [2][ny][nx] (compute type);
+ * kind 1: 1/2 sum rho |u|^2 (d_u_target unused).  Synchronises. */
+lbm_status lbm_loss(lbm_ctx *ctx, int kind, const void *d_u_target, double *h_loss);
+
+/* Native checkpoints: the lattice the next step reads, in the storage
+ * layout and type, plus nothing else (the AA phase is part of the context;
+ * checkpoints need the two-lattice pattern).  *bytes = one state. */
+lbm_status lbm_state_bytes(const lbm_ctx *ctx, size_t *bytes);
+lbm_status lbm_save_state(lbm_ctx *ctx, void *d_dst);
+lbm_status lbm_load_state(lbm_ctx *ctx, const void *d_src);
+
+/* Forward recompute for the adjoint: runs n steps from native state
+ * d_states[0] and writes A_{k+1} into d_states[k+1] (k = 0..n-1);
+ * h_states is a HOST array of n+1 device pointers.  The context's own
+ * lattice is not touched.  Two-lattice dense only. */
+lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n);
+
+/* Discrete adjoint of n steps (transpose of the linearised Algorithm 1
+ * step, with the bounce-back gather transposed into a push).
+ * h_states: HOST array of n device pointers to native states A_{t0+k}.
+ * d_lambda [9][ny][nx] compute type: in dL/dA_{t0+n}, out dL/dA_{t0};
+ * d_lambda_tmp: same size, scratch.  d_grad_force [2][ny][nx] compute type,
+ * accumulated (+=): dL/dF(x) for the per-node force (the uniform force's
+ * gradient is its node sum).  Entries of solid nodes come out 0.
+ * LBM_ERR_UNSUPPORTED unless dense and two-lattice. */
+lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n,
+                        void *d_lambda, void *d_lambda_tmp, void *d_grad_force);
+
+/* Transpose of lbm_macros at the current state: from dL/drho [ny][nx] and
+ * dL/du [2][ny][nx] (compute type, either NULL = 0) writes
+ * d_lambda = dL/dA_t [9][ny][nx] and accumulates dL/dF into d_grad_force
+ * (+=, may be NULL).  Dense two-lattice only. */
+lbm_status lbm_macros_backward(lbm_ctx *ctx, const void *d_grad_rho, const void *d_grad_u,
+                               void *d_lambda, void *d_grad_force);
+
+/* Host copies of the geometry tables: link mask [ny][nx] (see lbm_create),
+ * and for the sparse layout tile_id [ceil(ny/16)][ceil(nx/16)] (compact
+ * tile number in row-major tile order, -1 absent) and nbr [ntiles][9]
+ * (tile at offset c_i, wrapped on periodic axes, -1 beyond a wall or
+ * absent).  Any output may be NULL; lbm_tile_map returns
+ * LBM_ERR_UNSUPPORTED for the dense layout. */
+lbm_status lbm_link_mask(const lbm_ctx *ctx, uint8_t *h_mask);
+lbm_status lbm_tile_map(const lbm_ctx *ctx, int32_t *h_tile_id, int32_t *h_nbr, int *h_ntiles);
+
+/* Host-only: the same link mask and tile tables lbm_create would build for
+ * p (no device work, no context).  h_mask [ny][nx]; h_tile_id and h_nbr as
+ * for lbm_tile_map (sparse layout only; may be NULL); *h_nfluid = fluid
+ * nodes.  Lets a caller (or a test without a GPU) inspect the geometry. */
+lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id, int32_t *h_nbr,
+                        int *h_ntiles, long long *h_nfluid);
+
+long long lbm_fluid_nodes(const lbm_ctx *ctx);
+long long lbm_step_count(const lbm_ctx *ctx);
+const char *lbm_status_string(lbm_status s);
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

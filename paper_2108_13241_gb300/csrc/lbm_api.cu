@@ -1,0 +1,531 @@
+// lbm_api.cu -- the C ABI of include/lbm.h: argument checks, the host context,
+// workspace carving, lattice-phase bookkeeping and kernel dispatch.
+//
+// Lattice phases (how the device lattice holds the state A_t):
+//   two-lattice: lat[cur] holds A_t in slot order (PH_PLAIN); a step reads
+//     lat[cur], writes lat[1-cur] and flips cur (Algorithm 1 with the swap
+//     done by exchanging pointers, not by a copy kernel).
+//   AA: one lattice.  PH_SWAPPED: slot opp(i) of x holds A_i(x).  A
+//     gather/scatter step moves it to PH_STREAMED (slot i of x holds the
+//     pulled f'_i(x) of the next step); a local step moves it back.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params p;
+    Geo geo;
+    Phys phys;
+    size_t esize;      // bytes per stored value
+    size_t csize;      // bytes per compute value
+    long long nfluid;
+    std::vector<uint8_t> mask;    // canonical link mask [ny][nx]
+    std::vector<int32_t> tile_id; // [nty][ntx]
+    std::vector<int32_t> nbr;     // [ntiles][9], D2Q9 order
+    void *lat[2];
+    size_t lat_bytes;
+    double *partial;
+    double *red_out;
+    int cur;
+    int phase;
+    long long steps;
+    cudaStream_t stream;
+    lbm_status sticky;
+    std::string err;
+};
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t elem_size(int prec) { return prec == LBM_F64 ? 8 : (prec == LBM_F32 ? 4 : 2); }
+size_t comp_size(int prec) { return prec == LBM_F64 ? 8 : 4; }
+
+const char *check_params(const lbm_params *p) {
+    if (!p) return "params is NULL";
+    if (p->nx < 16 || p->nx % 16) return "nx must be a positive multiple of 16";
+    if (p->ny < 1) return "ny must be >= 1";
+    if ((long long)p->nx * p->ny > (1ll << 30)) return "nx*ny must be <= 2^30";
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be > 0.5";
+    if (!std::isfinite(p->fx) || !std::isfinite(p->fy)) return "force must be finite";
+    if ((p->west.periodic != 0) != (p->east.periodic != 0))
+        return "west and east must both be periodic or both be walls";
+    if ((p->south.periodic != 0) != (p->north.periodic != 0))
+        return "south and north must both be periodic or both be walls";
+    if (p->precision < LBM_F64 || p->precision > LBM_F16S) return "unknown precision";
+    if (p->layout != LBM_DENSE && p->layout != LBM_SPARSE_TILE16) return "unknown layout";
+    if (p->pattern != LBM_TWO_LATTICE && p->pattern != LBM_AA) return "unknown pattern";
+    if (p->layout == LBM_SPARSE_TILE16 && p->south.periodic && p->ny % 16)
+        return "sparse layout with a periodic y axis needs ny % 16 == 0";
+    const lbm_side *s[4] = {&p->west, &p->east, &p->south, &p->north};
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(s[k]->ux) || !std::isfinite(s[k]->uy)) return "wall velocity must be finite";
+    return nullptr;
+}
+
+struct Plan {
+    long long nfluid;
+    int ntiles, ntx, nty;
+    bool has_mask;
+    long long nslot;
+    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, total;
+    size_t lat_bytes, mask_bytes;
+};
+
+// Geometry tables and the workspace layout for p.
+void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int32_t> &tile_id,
+               std::vector<int32_t> &nbr, std::vector<int32_t> &txy, Plan &pl) {
+    const long long N = (long long)p.nx * p.ny;
+    mask.assign((size_t)N, 0);
+    pl.nfluid = build_link_mask(p, mask.data());
+    bool any = false;
+    for (long long n = 0; n < N && !any; ++n) any = mask[(size_t)n] != 0;
+    pl.ntx = (p.nx + TILE - 1) / TILE;
+    pl.nty = (p.ny + TILE - 1) / TILE;
+    pl.ntiles = 0;
+    if (p.layout == LBM_SPARSE_TILE16) {
+        tile_id.assign((size_t)pl.ntx * pl.nty, -1);
+        txy.assign((size_t)pl.ntx * pl.nty, 0);
+        nbr.assign((size_t)pl.ntx * pl.nty * 9, -1);
+        pl.ntiles = build_tile_map(p, mask.data(), tile_id.data(), nbr.data(), txy.data());
+        txy.resize((size_t)pl.ntiles);
+        nbr.resize((size_t)pl.ntiles * 9);
+        pl.has_mask = true;
+        pl.nslot = (long long)pl.ntiles * TILE_N;
+    } else {
+        pl.has_mask = any;
+        pl.nslot = N;
+    }
+    const size_t es = elem_size(p.precision);
+    pl.lat_bytes = (size_t)9 * (size_t)pl.nslot * es;
+    size_t off = align256(pl.lat_bytes);
+    pl.off_lat1 = off;
+    if (p.pattern == LBM_TWO_LATTICE) off += align256(pl.lat_bytes);
+    pl.off_mask = off;
+    pl.mask_bytes = p.layout == LBM_SPARSE_TILE16 ? (size_t)pl.ntiles * TILE_N : (pl.has_mask ? (size_t)N : 0);
+    off += align256(pl.mask_bytes);
+    pl.off_nbr = off;
+    if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntiles * 9 * 4);
+    pl.off_txy = off;
+    if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntiles * 4);
+    pl.off_tid = off;
+    if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntx * pl.nty * 4);
+    pl.off_part = off;
+    off += align256((size_t)RED_BLOCKS * 4 * sizeof(double));
+    pl.off_out = off;
+    off += align256(4 * sizeof(double));
+    pl.total = off;
+}
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg) {
+    if (c) {
+        if (s == LBM_ERR_CUDA) c->sticky = s;
+        c->err = msg;
+    }
+    return s;
+}
+
+lbm_status cuda_check(lbm_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LBM_OK;
+    return fail(c, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_DISPATCH(prec, expr)                       \
+    ([&]() -> cudaError_t {                            \
+        switch (prec) {                                \
+        case LBM_F64: { constexpr int P = LBM_F64; return expr; } \
+        case LBM_F32: { constexpr int P = LBM_F32; return expr; } \
+        default: { constexpr int P = LBM_F16S; return expr; }     \
+        }                                              \
+    }())
+
+#define LBM_CTX_CHECK(ctx)                                   \
+    do {                                                     \
+        if (!(ctx)) return LBM_ERR_INVALID;                  \
+        if ((ctx)->sticky != LBM_OK) return (ctx)->sticky;   \
+    } while (0)
+
+void set_force_mode(lbm_ctx *c) {
+    if (c->phys.force) c->phys.force_mode = FORCE_FIELD;
+    else if (c->phys.fx != 0.0 || c->phys.fy != 0.0) c->phys.force_mode = FORCE_UNIFORM;
+    else c->phys.force_mode = FORCE_NONE;
+}
+
+void *current_lattice(lbm_ctx *c) { return c->p.pattern == LBM_AA ? c->lat[0] : c->lat[c->cur]; }
+int current_phase(lbm_ctx *c) { return c->p.pattern == LBM_AA ? c->phase : PH_PLAIN; }
+
+} // namespace
+
+extern "C" {
+
+const char *lbm_status_string(lbm_status s) {
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_OOM: return "workspace too small";
+    case LBM_ERR_DIVERGED: return "diverged (NaN/Inf)";
+    case LBM_ERR_TIMEOUT: return "timeout";
+    case LBM_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes) {
+    if (!bytes || check_params(p)) return LBM_ERR_INVALID;
+    std::vector<uint8_t> mask;
+    std::vector<int32_t> tid, nbr, txy;
+    Plan pl;
+    make_plan(*p, mask, tid, nbr, txy, pl);
+    *bytes = pl.total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_ctx **out) {
+    if (!out) return LBM_ERR_INVALID;
+    *out = nullptr;
+    if (check_params(p)) return LBM_ERR_INVALID;
+    if (!d_workspace || ((uintptr_t)d_workspace & 255)) return LBM_ERR_INVALID;
+    lbm_ctx *c = new lbm_ctx();
+    c->p = *p;
+    c->p.solid = nullptr;
+    c->stream = (cudaStream_t)p->stream;
+    c->sticky = LBM_OK;
+    std::vector<int32_t> txy;
+    Plan pl;
+    make_plan(*p, c->mask, c->tile_id, c->nbr, txy, pl);
+    if (bytes < pl.total) {
+        delete c;
+        return LBM_ERR_OOM;
+    }
+    c->esize = elem_size(p->precision);
+    c->csize = comp_size(p->precision);
+    c->nfluid = pl.nfluid;
+    c->lat_bytes = pl.lat_bytes;
+    char *ws = reinterpret_cast<char *>(d_workspace);
+    c->lat[0] = ws;
+    c->lat[1] = p->pattern == LBM_TWO_LATTICE ? ws + pl.off_lat1 : ws;
+    c->partial = reinterpret_cast<double *>(ws + pl.off_part);
+    c->red_out = reinterpret_cast<double *>(ws + pl.off_out);
+    c->cur = 0;
+    c->phase = p->pattern == LBM_AA ? PH_SWAPPED : PH_PLAIN;
+    c->steps = 0;
+
+    Geo &g = c->geo;
+    std::memset(&g, 0, sizeof(g));
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.periodic_x = p->west.periodic != 0;
+    g.periodic_y = p->south.periodic != 0;
+    g.layout = p->layout;
+    g.ntx = pl.ntx;
+    g.nty = pl.nty;
+    g.ntiles = pl.ntiles;
+    g.nslot = pl.nslot;
+    g.nnode = (long long)p->nx * p->ny;
+    g.has_mask = pl.has_mask;
+    g.mask = pl.mask_bytes ? reinterpret_cast<const uint8_t *>(ws + pl.off_mask) : nullptr;
+
+    Phys &ph = c->phys;
+    std::memset(&ph, 0, sizeof(ph));
+    ph.omega = 1.0 / p->tau;
+    ph.fx = p->fx;
+    ph.fy = p->fy;
+    const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const lbm_side *sides[4] = {&p->west, &p->east, &p->south, &p->north};
+    for (int s = 0; s < 4; ++s)
+        for (int i = 0; i < 9; ++i) {
+            // half-way bounce-back on a wall moving at u_w, rho_w = rho_0 = 1
+            ph.wt[s][i] = sides[s]->periodic ? 0.0 : 6.0 * W[i] * (CX[i] * sides[s]->ux + CY[i] * sides[s]->uy);
+            if (ph.wt[s][i] != 0.0) ph.has_wall = 1;
+        }
+    set_force_mode(c);
+
+    lbm_status st = LBM_OK;
+    cudaStream_t s = c->stream;
+    st = cuda_check(c, cudaMemsetAsync(c->lat[0], 0, pl.lat_bytes, s), "memset lattice");
+    if (!st && p->pattern == LBM_TWO_LATTICE)
+        st = cuda_check(c, cudaMemsetAsync(c->lat[1], 0, pl.lat_bytes, s), "memset lattice");
+    if (!st && p->layout == LBM_DENSE && pl.mask_bytes)
+        st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_mask, c->mask.data(), pl.mask_bytes,
+                                           cudaMemcpyHostToDevice, s), "copy mask");
+    std::vector<uint8_t> tmask;
+    std::vector<int32_t> nbr3;
+    if (!st && p->layout == LBM_SPARSE_TILE16 && pl.ntiles > 0) {
+        tmask.resize((size_t)pl.ntiles * TILE_N);
+        build_tile_masks(*p, c->mask.data(), txy.data(), pl.ntiles, tmask.data());
+        // device neighbour table in 3x3 order: [t][3*(oy+1) + (ox+1)]
+        nbr3.resize((size_t)pl.ntiles * 9);
+        for (int t = 0; t < pl.ntiles; ++t)
+            for (int i = 0; i < 9; ++i)
+                nbr3[(size_t)t * 9 + 3 * (CY[i] + 1) + (CX[i] + 1)] = c->nbr[(size_t)t * 9 + i];
+        st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_mask, tmask.data(), tmask.size(),
+                                           cudaMemcpyHostToDevice, s), "copy tile masks");
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_nbr, nbr3.data(), nbr3.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy neighbour table");
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_txy, txy.data(), txy.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy tile coordinates");
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_tid, c->tile_id.data(), c->tile_id.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy tile ids");
+        g.nbr = reinterpret_cast<const int32_t *>(ws + pl.off_nbr);
+        g.tile_xy = reinterpret_cast<const int32_t *>(ws + pl.off_txy);
+        g.tile_id = reinterpret_cast<const int32_t *>(ws + pl.off_tid);
+    } else if (p->layout == LBM_SPARSE_TILE16) {
+        g.tile_id = reinterpret_cast<const int32_t *>(ws + pl.off_tid);
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_tid, c->tile_id.data(), c->tile_id.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy tile ids");
+    }
+    if (!st)
+        st = cuda_check(c, LBM_DISPATCH(p->precision, launch_init<P>(g, current_phase(c), nullptr, nullptr,
+                                                                     current_lattice(c), s)),
+                        "init kernel");
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "create sync");
+    if (st) {
+        delete c;
+        return st;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx *ctx) {
+    if (!ctx) return LBM_ERR_INVALID;
+    delete ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force(lbm_ctx *ctx, const void *d_force) {
+    LBM_CTX_CHECK(ctx);
+    if (d_force && ((uintptr_t)d_force & 15)) return fail(ctx, LBM_ERR_INVALID, "force not 16-byte aligned");
+    ctx->phys.force = d_force;
+    set_force_mode(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *d_rho, const void *d_u) {
+    LBM_CTX_CHECK(ctx);
+    if (ctx->p.pattern == LBM_AA) ctx->phase = PH_SWAPPED;
+    ctx->steps = 0;
+    const Geo &g = ctx->geo;
+    return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision, launch_init<P>(g, current_phase(ctx), d_rho, d_u,
+                                                                         current_lattice(ctx), ctx->stream)),
+                      "init kernel");
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int n) {
+    LBM_CTX_CHECK(ctx);
+    if (n < 0) return fail(ctx, LBM_ERR_INVALID, "negative step count");
+    const Geo &g = ctx->geo;
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e;
+        if (ctx->p.pattern == LBM_TWO_LATTICE) {
+            const void *a = ctx->lat[ctx->cur];
+            void *b = ctx->lat[1 - ctx->cur];
+            e = LBM_DISPATCH(ctx->p.precision,
+                             launch_step<P>(g, ctx->phys, MODE_TWO_LATTICE, a, b, ctx->stream));
+            ctx->cur = 1 - ctx->cur;
+        } else {
+            const int mode = ctx->phase == PH_SWAPPED ? MODE_AA_PULLPUSH : MODE_AA_LOCAL;
+            e = LBM_DISPATCH(ctx->p.precision,
+                             launch_step<P>(g, ctx->phys, mode, ctx->lat[0], ctx->lat[0], ctx->stream));
+            ctx->phase = ctx->phase == PH_SWAPPED ? PH_STREAMED : PH_SWAPPED;
+        }
+        if (e != cudaSuccess) return cuda_check(ctx, e, "step kernel");
+        ++ctx->steps;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_macros(lbm_ctx *ctx, void *d_rho, void *d_u) {
+    LBM_CTX_CHECK(ctx);
+    if (!d_rho && !d_u) return LBM_OK;
+    return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision,
+                                        launch_macros<P>(ctx->geo, ctx->phys, current_phase(ctx),
+                                                         current_lattice(ctx), d_rho, d_u, ctx->stream)),
+                      "macros kernel");
+}
+
+lbm_status lbm_get_f(lbm_ctx *ctx, void *d_f) {
+    LBM_CTX_CHECK(ctx);
+    if (!d_f) return fail(ctx, LBM_ERR_INVALID, "d_f is NULL");
+    return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision, launch_get_f<P>(ctx->geo, current_phase(ctx),
+                                                                          current_lattice(ctx), d_f,
+                                                                          ctx->stream)),
+                      "get_f kernel");
+}
+
+lbm_status lbm_set_f(lbm_ctx *ctx, const void *d_f) {
+    LBM_CTX_CHECK(ctx);
+    if (!d_f) return fail(ctx, LBM_ERR_INVALID, "d_f is NULL");
+    if (ctx->p.pattern == LBM_AA) ctx->phase = PH_SWAPPED;
+    return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision, launch_set_f<P>(ctx->geo, current_phase(ctx), d_f,
+                                                                          current_lattice(ctx), ctx->stream)),
+                      "set_f kernel");
+}
+
+static lbm_status run_reduce(lbm_ctx *ctx, int kind, const void *target, double out[4]) {
+    lbm_status st = cuda_check(
+        ctx, LBM_DISPATCH(ctx->p.precision, launch_reduce<P>(ctx->geo, ctx->phys, current_phase(ctx), kind,
+                                                             current_lattice(ctx), target, ctx->partial,
+                                                             ctx->red_out, ctx->stream)),
+        "reduce kernel");
+    if (st) return st;
+    st = cuda_check(ctx, cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                         ctx->stream), "reduce copy");
+    if (st) return st;
+    return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "reduce sync");
+}
+
+lbm_status lbm_reduce(lbm_ctx *ctx, double *h_mass, double h_mom[2]) {
+    LBM_CTX_CHECK(ctx);
+    double out[4];
+    lbm_status st = run_reduce(ctx, 0, nullptr, out);
+    if (st) return st;
+    // canonical values are w_i + shifted value; sum_i w_i = 1, sum_i c_i w_i = 0
+    const double mass = (double)ctx->nfluid + out[0];
+    if (h_mass) *h_mass = mass;
+    if (h_mom) {
+        h_mom[0] = out[1];
+        h_mom[1] = out[2];
+    }
+    if (!std::isfinite(mass) || !std::isfinite(out[1]) || !std::isfinite(out[2]))
+        return fail(ctx, LBM_ERR_DIVERGED, "non-finite mass or momentum");
+    return LBM_OK;
+}
+
+lbm_status lbm_loss(lbm_ctx *ctx, int kind, const void *d_u_target, double *h_loss) {
+    LBM_CTX_CHECK(ctx);
+    if (!h_loss || (kind != 0 && kind != 1) || (kind == 0 && !d_u_target))
+        return fail(ctx, LBM_ERR_INVALID, "bad loss arguments");
+    double out[4];
+    lbm_status st = run_reduce(ctx, kind == 0 ? 1 : 2, d_u_target, out);
+    if (st) return st;
+    *h_loss = kind == 0 ? (ctx->nfluid ? out[0] / (double)ctx->nfluid : 0.0) : out[0];
+    if (!std::isfinite(*h_loss)) return fail(ctx, LBM_ERR_DIVERGED, "non-finite loss");
+    return LBM_OK;
+}
+
+lbm_status lbm_state_bytes(const lbm_ctx *ctx, size_t *bytes) {
+    if (!ctx || !bytes) return LBM_ERR_INVALID;
+    *bytes = ctx->lat_bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx *ctx, void *d_dst) {
+    LBM_CTX_CHECK(ctx);
+    if (ctx->p.pattern != LBM_TWO_LATTICE) return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints need two-lattice");
+    if (!d_dst) return fail(ctx, LBM_ERR_INVALID, "d_dst is NULL");
+    return cuda_check(ctx, cudaMemcpyAsync(d_dst, ctx->lat[ctx->cur], ctx->lat_bytes, cudaMemcpyDeviceToDevice,
+                                           ctx->stream), "save state");
+}
+
+lbm_status lbm_load_state(lbm_ctx *ctx, const void *d_src) {
+    LBM_CTX_CHECK(ctx);
+    if (ctx->p.pattern != LBM_TWO_LATTICE) return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints need two-lattice");
+    if (!d_src) return fail(ctx, LBM_ERR_INVALID, "d_src is NULL");
+    return cuda_check(ctx, cudaMemcpyAsync(ctx->lat[ctx->cur], d_src, ctx->lat_bytes, cudaMemcpyDeviceToDevice,
+                                           ctx->stream), "load state");
+}
+
+lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n) {
+    LBM_CTX_CHECK(ctx);
+    if (ctx->p.pattern != LBM_TWO_LATTICE) return fail(ctx, LBM_ERR_UNSUPPORTED, "needs two-lattice");
+    if (n < 0 || (n > 0 && !h_states)) return fail(ctx, LBM_ERR_INVALID, "bad state list");
+    for (int k = 0; k < n; ++k) {
+        if (!h_states[k] || !h_states[k + 1] || ((uintptr_t)h_states[k] & 15) || ((uintptr_t)h_states[k + 1] & 15))
+            return fail(ctx, LBM_ERR_INVALID, "bad state pointer");
+        cudaError_t e = LBM_DISPATCH(ctx->p.precision, launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE,
+                                                                      h_states[k], h_states[k + 1], ctx->stream));
+        if (e != cudaSuccess) return cuda_check(ctx, e, "forward_states kernel");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n, void *d_lambda, void *d_lambda_tmp,
+                        void *d_grad_force) {
+    LBM_CTX_CHECK(ctx);
+    if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
+    if (n < 0 || (n > 0 && (!h_states || !d_lambda || !d_lambda_tmp || !d_grad_force)))
+        return fail(ctx, LBM_ERR_INVALID, "bad backward arguments");
+    if (((uintptr_t)d_lambda & 15) || ((uintptr_t)d_lambda_tmp & 15) || ((uintptr_t)d_grad_force & 15))
+        return fail(ctx, LBM_ERR_INVALID, "buffers must be 16-byte aligned");
+    void *in = d_lambda, *out = d_lambda_tmp;
+    for (int t = n - 1; t >= 0; --t) {
+        if (!h_states[t]) return fail(ctx, LBM_ERR_INVALID, "NULL state");
+        cudaError_t e = LBM_DISPATCH(ctx->p.precision, launch_adjoint<P>(ctx->geo, ctx->phys, h_states[t], in,
+                                                                         out, d_grad_force, ctx->stream));
+        if (e != cudaSuccess) return cuda_check(ctx, e, "adjoint kernel");
+        void *tmp = in;
+        in = out;
+        out = tmp;
+    }
+    if (in != d_lambda)
+        return cuda_check(ctx, cudaMemcpyAsync(d_lambda, in, (size_t)9 * ctx->geo.nnode * ctx->csize,
+                                               cudaMemcpyDeviceToDevice, ctx->stream), "lambda copy");
+    return LBM_OK;
+}
+
+lbm_status lbm_macros_backward(lbm_ctx *ctx, const void *d_grad_rho, const void *d_grad_u, void *d_lambda,
+                               void *d_grad_force) {
+    LBM_CTX_CHECK(ctx);
+    if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
+    if (!d_lambda) return fail(ctx, LBM_ERR_INVALID, "d_lambda is NULL");
+    return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision,
+                                        launch_macros_adjoint<P>(ctx->geo, ctx->phys, ctx->lat[ctx->cur],
+                                                                 d_grad_rho, d_grad_u, d_lambda, d_grad_force,
+                                                                 ctx->stream)),
+                      "macros adjoint kernel");
+}
+
+lbm_status lbm_link_mask(const lbm_ctx *ctx, uint8_t *h_mask) {
+    if (!ctx || !h_mask) return LBM_ERR_INVALID;
+    std::memcpy(h_mask, ctx->mask.data(), ctx->mask.size());
+    return LBM_OK;
+}
+
+lbm_status lbm_tile_map(const lbm_ctx *ctx, int32_t *h_tile_id, int32_t *h_nbr, int *h_ntiles) {
+    if (!ctx) return LBM_ERR_INVALID;
+    if (ctx->p.layout != LBM_SPARSE_TILE16) return LBM_ERR_UNSUPPORTED;
+    if (h_tile_id) std::memcpy(h_tile_id, ctx->tile_id.data(), ctx->tile_id.size() * 4);
+    if (h_nbr) std::memcpy(h_nbr, ctx->nbr.data(), ctx->nbr.size() * 4);
+    if (h_ntiles) *h_ntiles = ctx->geo.ntiles;
+    return LBM_OK;
+}
+
+lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id, int32_t *h_nbr,
+                        int *h_ntiles, long long *h_nfluid) {
+    if (check_params(p)) return LBM_ERR_INVALID;
+    std::vector<uint8_t> mask;
+    std::vector<int32_t> tid, nbr, txy;
+    Plan pl;
+    make_plan(*p, mask, tid, nbr, txy, pl);
+    if (h_mask) std::memcpy(h_mask, mask.data(), mask.size());
+    if (p->layout == LBM_SPARSE_TILE16) {
+        if (h_tile_id) std::memcpy(h_tile_id, tid.data(), tid.size() * 4);
+        if (h_nbr) std::memcpy(h_nbr, nbr.data(), nbr.size() * 4);
+        if (h_ntiles) *h_ntiles = pl.ntiles;
+    } else if (h_ntiles) {
+        *h_ntiles = 0;
+    }
+    if (h_nfluid) *h_nfluid = pl.nfluid;
+    return LBM_OK;
+}
+
+long long lbm_fluid_nodes(const lbm_ctx *ctx) { return ctx ? ctx->nfluid : -1; }
+long long lbm_step_count(const lbm_ctx *ctx) { return ctx ? ctx->steps : -1; }
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+} // extern "C"

@@ -1,0 +1,100 @@
+// lbm_internal.h -- declarations shared by the C-ABI layer (lbm_api.cu) and
+// the per-precision kernel translation units (kern_*.cu).  Not public.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int TILE = 16;        // sparse tile edge (nodes)
+constexpr int TILE_N = 256;     // nodes per tile
+constexpr int STEP_BLOCK = 256; // threads per block of the step kernels
+constexpr int AUX_BLOCK = 256;  // threads per block of the per-node kernels
+constexpr int RED_BLOCKS = 608; // blocks of the reduction pass (4 x 152 SMs)
+constexpr int WALL_SIDES = 5;   // W, E, S, N, and "solid obstacle" (term 0)
+
+// Kernel kinds of one time step.
+enum StepMode {
+    MODE_TWO_LATTICE = 0, // gather from src, store aligned into dst
+    MODE_AA_PULLPUSH = 1, // in place, from the swapped state: gather+scatter
+    MODE_AA_LOCAL = 2     // in place, from the streamed state: local only
+};
+
+// How the lattice currently holds A_t (see lbm_api.cu).
+enum Phase {
+    PH_PLAIN = 0,   // slot i at x holds A_i(x)                 (two-lattice)
+    PH_SWAPPED = 1, // slot opp(i) at x holds A_i(x)            (AA, even)
+    PH_STREAMED = 2 // slot i at x holds f'_i(x) (pre-collision) (AA, odd)
+};
+
+enum ForceMode { FORCE_NONE = 0, FORCE_UNIFORM = 1, FORCE_FIELD = 2 };
+
+// Geometry as the kernels see it (device pointers into the workspace).
+struct Geo {
+    int nx, ny;
+    int periodic_x, periodic_y;
+    int layout;            // lbm_layout
+    int ntx, nty, ntiles;  // sparse tile grid / kept tiles
+    long long nslot;       // elements per distribution slot (dense: nx*ny)
+    long long nnode;       // nx*ny: component stride of canonical arrays
+    const uint8_t *mask;   // dense [ny][nx]; sparse [ntiles][256]
+    const int32_t *nbr;    // sparse [ntiles][9]
+    const int32_t *tile_xy;// sparse [ntiles]: (ty << 16) | tx
+    const int32_t *tile_id;// sparse [nty][ntx]
+    int has_mask;          // 0: every node fluid, both axes periodic
+};
+
+// Physics as the kernels see it.
+struct Phys {
+    double omega;
+    double fx, fy;
+    const void *force;     // FORCE_FIELD: [2][ny][nx] compute type
+    int force_mode;
+    int has_wall;          // some wall term is nonzero
+    double wt[WALL_SIDES][9];
+};
+
+// Launchers, defined in lbm_kernels.cuh and instantiated per precision P
+// (an lbm_precision value) in kern_f64.cu, kern_f32.cu, kern_f16s.cu.
+template <int P> cudaError_t launch_step(const Geo &g, const Phys &ph, int mode,
+                                         const void *src, void *dst, cudaStream_t s);
+template <int P> cudaError_t launch_init(const Geo &g, int phase, const void *rho,
+                                         const void *u, void *lat, cudaStream_t s);
+template <int P> cudaError_t launch_set_f(const Geo &g, int phase, const void *f, void *lat,
+                                          cudaStream_t s);
+template <int P> cudaError_t launch_get_f(const Geo &g, int phase, const void *lat, void *f,
+                                          cudaStream_t s);
+template <int P> cudaError_t launch_macros(const Geo &g, const Phys &ph, int phase,
+                                           const void *lat, void *rho, void *u,
+                                           cudaStream_t s);
+// FP64 partial sums -> partial[RED_BLOCKS][4], then a fixed-order final sum
+// into out[4].  kind: 0 mass/momentum of A_t; 1 MSE vs target; 2 kinetic
+// energy.
+template <int P> cudaError_t launch_reduce(const Geo &g, const Phys &ph, int phase, int kind,
+                                           const void *lat, const void *target,
+                                           double *partial, double *out, cudaStream_t s);
+template <int P> cudaError_t launch_adjoint(const Geo &g, const Phys &ph, const void *state,
+                                            const void *lam_in, void *lam_out,
+                                            void *grad_force, cudaStream_t s);
+template <int P> cudaError_t launch_macros_adjoint(const Geo &g, const Phys &ph,
+                                                   const void *state, const void *g_rho,
+                                                   const void *g_u, void *lam,
+                                                   void *grad_force, cudaStream_t s);
+
+// Host geometry preparation (lbm_geometry.cpp).
+// Link mask: bit (i-1) set iff link i pulls from a solid node or across a
+// wall; 0xFF for solid nodes and for fluid nodes with no link to any node.
+long long build_link_mask(const lbm_params &p, uint8_t *mask);
+// Tile map (16x16): tile_id[nty][ntx] (-1 absent), nbr[ntiles][9],
+// tile_xy[ntiles].  Returns the number of kept tiles.
+int build_tile_map(const lbm_params &p, const uint8_t *mask, int32_t *tile_id,
+                   int32_t *nbr, int32_t *tile_xy);
+// Per-tile masks [ntiles][256] from the canonical mask (0xFF outside).
+void build_tile_masks(const lbm_params &p, const uint8_t *mask, const int32_t *tile_xy,
+                      int ntiles, uint8_t *tile_mask);
+
+} // namespace lbm

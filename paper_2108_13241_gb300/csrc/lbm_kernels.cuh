@@ -1,0 +1,1090 @@
+// lbm_kernels.cuh -- CUDA kernels of the D2Q9 BGK stream-and-collide update
+// for sm_103a, templated on the storage precision.  Included only by the
+// per-precision translation units kern_f64.cu, kern_f32.cu, kern_f16s.cu.
+//
+// The hot kernel (k_step) is Algorithm 1's fused pull kernel (Sec. 3):
+// gather f'_i = A_i(x - c_i) with half-way bounce-back, moments (Eq. rho, v),
+// equilibrium (Eq. f^eq), BGK relaxation (Eq. LBM, Eq. Omega^BGK) with a Guo
+// body-force source, aligned store.  Design for GB300:
+//  * SoA slots, one 16-byte vector per thread and slot: VEC = 2 (FP64),
+//    4 (FP32) or 8 (FP16-shifted) consecutive nodes along x;
+//  * the x-shifted pulls (c_x != 0, the uncoalesced loads Sec. 4.2.1
+//    reports) take the aligned vector and one value from the neighbouring
+//    lane (__shfl_up/down_sync); only lanes at a warp or row edge load that
+//    value from memory (an L1/L2 hit);
+//  * a per-node link mask (one byte) selects a divergent slow path only at
+//    nodes next to walls or obstacles; all-solid vectors move no data;
+//  * distributions are stored shifted, f_i - w_i, and the collision runs in
+//    shifted variables (rho = 1 + sum, m = sum c_i (f_i - w_i)), so FP32 and
+//    FP16 keep their mantissa for the small deviations from rest;
+//  * every variant (dense / tiled, two-lattice / AA) feeds the same
+//    `collide` with the same operands, so FP64 variants agree bit for bit.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+#define LBM_FULL 0xffffffffu
+
+// ------------------------------------------------------------- lattice
+
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+template <class C> __host__ __device__ constexpr C wgt(int i) {
+    return i == 0 ? C(4.0 / 9.0) : (i <= 4 ? C(1.0 / 9.0) : C(1.0 / 36.0));
+}
+
+// ------------------------------------------------------------- storage
+
+template <int P> struct St;
+template <> struct St<LBM_F64> {
+    typedef double R; // stored element
+    typedef double C; // compute type
+    enum { VEC = 2 };
+    static __device__ __forceinline__ C dec(R r) { return r; }
+    static __device__ __forceinline__ R enc(C c) { return c; }
+};
+template <> struct St<LBM_F32> {
+    typedef float R;
+    typedef float C;
+    enum { VEC = 4 };
+    static __device__ __forceinline__ C dec(R r) { return r; }
+    static __device__ __forceinline__ R enc(C c) { return c; }
+};
+template <> struct St<LBM_F16S> {
+    typedef unsigned short R; // binary16 bits of f_i - w_i
+    typedef float C;
+    enum { VEC = 8 };
+    static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)); }
+    static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c)); }
+};
+
+template <class R, int VEC> union V16 {
+    uint4 u;
+    R v[VEC];
+};
+
+template <bool NC, class R, int VEC>
+__device__ __forceinline__ V16<R, VEC> ld16(const R *p) {
+    V16<R, VEC> r;
+    if (NC)
+        r.u = __ldg(reinterpret_cast<const uint4 *>(p));
+    else
+        r.u = *reinterpret_cast<const uint4 *>(p);
+    return r;
+}
+template <bool NC, class R> __device__ __forceinline__ R ld1(const R *p) {
+    if (NC) return __ldg(p);
+    return *p;
+}
+template <> __device__ __forceinline__ unsigned short ld1<true, unsigned short>(const unsigned short *p) {
+    return __ldg(p);
+}
+template <class R, int VEC> __device__ __forceinline__ void st16(R *p, const V16<R, VEC> &v) {
+    *reinterpret_cast<uint4 *>(p) = v.u;
+}
+
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(LBM_FULL, v, 1); }
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(LBM_FULL, v, 1); }
+__device__ __forceinline__ unsigned short shfl_up1(unsigned short v) {
+    return (unsigned short)__shfl_up_sync(LBM_FULL, (unsigned)v, 1);
+}
+__device__ __forceinline__ double shfl_down1(double v) { return __shfl_down_sync(LBM_FULL, v, 1); }
+__device__ __forceinline__ float shfl_down1(float v) { return __shfl_down_sync(LBM_FULL, v, 1); }
+__device__ __forceinline__ unsigned short shfl_down1(unsigned short v) {
+    return (unsigned short)__shfl_down_sync(LBM_FULL, (unsigned)v, 1);
+}
+
+// VEC mask bytes of consecutive nodes, as one integer (node k in byte k).
+template <int VEC> __device__ __forceinline__ unsigned long long ld_mask(const uint8_t *p);
+template <> __device__ __forceinline__ unsigned long long ld_mask<2>(const uint8_t *p) {
+    return __ldg(reinterpret_cast<const unsigned short *>(p));
+}
+template <> __device__ __forceinline__ unsigned long long ld_mask<4>(const uint8_t *p) {
+    return __ldg(reinterpret_cast<const unsigned int *>(p));
+}
+template <> __device__ __forceinline__ unsigned long long ld_mask<8>(const uint8_t *p) {
+    return __ldg(reinterpret_cast<const unsigned long long *>(p));
+}
+template <int VEC> __host__ __device__ constexpr unsigned long long mask_ones() {
+    return VEC == 8 ? ~0ull : ((1ull << (8 * VEC)) - 1ull);
+}
+// bit b replicated into every node byte
+template <int VEC> __host__ __device__ constexpr unsigned long long mask_rep(int b) {
+    return VEC == 2 ? (0x0101ull << b) : (VEC == 4 ? (0x01010101ull << b) : (0x0101010101010101ull << b));
+}
+
+// ------------------------------------------------------------- addressing
+
+__device__ __forceinline__ int pick3(int o, int a, int b, int c) { return o < 0 ? a : (o > 0 ? c : b); }
+
+// Dense SoA f[slot][ny][nx]; thread = VEC nodes (x0..x0+VEC-1, y).
+template <int VEC> struct DenseAddr {
+    int x0, y, xv, nvx, nx, ny;
+    bool px, py, valid;
+    long long nslot;
+    const uint8_t *mask;
+
+    __device__ __forceinline__ DenseAddr(const Geo &g, long long gtid) {
+        nx = g.nx;
+        ny = g.ny;
+        px = g.periodic_x;
+        py = g.periodic_y;
+        nslot = g.nslot;
+        mask = g.mask;
+        nvx = nx / VEC;
+        const long long nvec = (long long)ny * nvx;
+        valid = gtid < nvec;
+        const long long v = valid ? gtid : nvec - 1;
+        y = (int)(v / nvx);
+        xv = (int)(v - (long long)y * nvx);
+        x0 = xv * VEC;
+    }
+    __device__ __forceinline__ int row(int dy) const {
+        int r = y + dy;
+        if (r < 0) r = py ? r + ny : 0;
+        else if (r >= ny) r = py ? r - ny : ny - 1;
+        return r;
+    }
+    __device__ __forceinline__ int col(int c) const {
+        if (c < 0) c = px ? c + nx : 0;
+        else if (c >= nx) c = px ? c - nx : nx - 1;
+        return c;
+    }
+    // aligned vector of slot at (x0, y + dy)
+    __device__ __forceinline__ long long vidx(int slot, int dy) const {
+        return slot * nslot + (long long)row(dy) * nx + x0;
+    }
+    // element (x0 + k + dx, y + dy), wrapped (periodic) or clamped (wall)
+    __device__ __forceinline__ long long eidx(int slot, int k, int dx, int dy) const {
+        return slot * nslot + (long long)row(dy) * nx + col(x0 + k + dx);
+    }
+    __device__ __forceinline__ bool left_in_warp(int lane) const { return lane > 0 && xv > 0; }
+    __device__ __forceinline__ bool right_in_warp(int lane) const { return lane < 31 && xv < nvx - 1; }
+    __device__ __forceinline__ int gx(int k) const { return x0 + k; }
+    __device__ __forceinline__ int gy() const { return y; }
+    __device__ __forceinline__ bool in_domain() const { return true; }
+    __device__ __forceinline__ long long node(int k) const { return (long long)y * nx + x0 + k; }
+    __device__ __forceinline__ const uint8_t *mask_ptr() const { return mask + (long long)y * nx + x0; }
+};
+
+// Tiled sparse f[tile][slot][16][16]; thread = VEC nodes of one tile row.
+// nbr3 is the device table [tile][3*(oy+1) + (ox+1)] (absent -> -1).
+template <int VEC> struct TileAddr {
+    enum { TPR = TILE / VEC, TPT = TILE * (TILE / VEC) };
+    int t, lx0, ly, xv, tx, ty, nx, ny;
+    bool valid;
+    int nb[9];
+    const uint8_t *mask;
+
+    __device__ __forceinline__ TileAddr(const Geo &g, long long gtid) {
+        nx = g.nx;
+        ny = g.ny;
+        mask = g.mask;
+        long long tt = gtid / TPT;
+        valid = tt < g.ntiles;
+        if (!valid) tt = g.ntiles - 1;
+        t = (int)tt;
+        const int tl = (int)(gtid - (gtid / TPT) * TPT);
+        ly = tl / TPR;
+        xv = tl - ly * TPR;
+        lx0 = xv * VEC;
+        const int txy = __ldg(g.tile_xy + t);
+        tx = txy & 0xFFFF;
+        ty = txy >> 16;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const int n = __ldg(g.nbr + 9 * (long long)t + j);
+            nb[j] = n < 0 ? t : n; // absent: any valid tile, the value is unused
+        }
+    }
+    __device__ __forceinline__ int tile_at(int ox, int oy) const {
+        return pick3(oy, pick3(ox, nb[0], nb[1], nb[2]), pick3(ox, nb[3], nb[4], nb[5]),
+                     pick3(ox, nb[6], nb[7], nb[8]));
+    }
+    __device__ __forceinline__ long long at(int slot, int c, int r) const {
+        const int ox = c < 0 ? -1 : (c >= TILE ? 1 : 0);
+        const int oy = r < 0 ? -1 : (r >= TILE ? 1 : 0);
+        const int tt = tile_at(ox, oy);
+        return ((long long)tt * 9 + slot) * TILE_N + (r & (TILE - 1)) * TILE + (c & (TILE - 1));
+    }
+    __device__ __forceinline__ long long vidx(int slot, int dy) const { return at(slot, lx0, ly + dy); }
+    __device__ __forceinline__ long long eidx(int slot, int k, int dx, int dy) const {
+        return at(slot, lx0 + k + dx, ly + dy);
+    }
+    __device__ __forceinline__ bool left_in_warp(int) const { return xv > 0; }
+    __device__ __forceinline__ bool right_in_warp(int) const { return xv < TPR - 1; }
+    __device__ __forceinline__ int gx(int k) const { return tx * TILE + lx0 + k; }
+    __device__ __forceinline__ int gy() const { return ty * TILE + ly; }
+    __device__ __forceinline__ bool in_domain() const { return gy() < ny; }
+    __device__ __forceinline__ long long node(int k) const { return (long long)gy() * nx + gx(k); }
+    __device__ __forceinline__ const uint8_t *mask_ptr() const {
+        return mask + (long long)t * TILE_N + ly * TILE + lx0;
+    }
+};
+
+// Which wall side link i of node (x, y) crosses (0 W, 1 E, 2 S, 3 N), or 4
+// when its source is an obstacle node.  The y side is examined first.
+__device__ __forceinline__ int wall_side(const Geo &g, int x, int y, int i) {
+    const int sy = y - cy(i);
+    if ((sy < 0 || sy >= g.ny) && !g.periodic_y) return sy < 0 ? 2 : 3;
+    const int sx = x - cx(i);
+    if ((sx < 0 || sx >= g.nx) && !g.periodic_x) return sx < 0 ? 0 : 1;
+    return 4;
+}
+
+// ------------------------------------------------------------- physics
+
+// Moments of the gathered shifted f' (Eq. rho, v; u shifted by F/2).
+template <class C, bool HAS_F>
+__device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rho, C &inv, C &ux,
+                                        C &uy) {
+    drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    rho = C(1) + drho;
+    const C mx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
+    const C my = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+    inv = C(1) / rho;
+    if (HAS_F) {
+        ux = (mx + C(0.5) * Fx) * inv;
+        uy = (my + C(0.5) * Fy) * inv;
+    } else {
+        ux = mx * inv;
+        uy = my * inv;
+    }
+}
+
+template <class C> struct Coef {
+    C om, om1, kk;
+    __device__ __forceinline__ explicit Coef(const Phys &ph)
+        : om(C(ph.omega)), om1(C(1) - C(ph.omega)), kk(C(1) - C(0.5) * C(ph.omega)) {}
+};
+
+// BGK relaxation with Guo source, in shifted variables, in place on f:
+//   f_i <- f_i + omega (f^eq_i - w_i - f_i) + S_i
+// evaluated pairwise over opposite links (c_opp = -c): the even part of
+// f^eq - w and S is shared, the odd part changes sign.
+template <class C, bool HAS_F>
+__device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
+    C drho, rho, inv, ux, uy;
+    moments<C, HAS_F>(f, Fx, Fy, drho, rho, inv, ux, uy);
+    const C usq = C(1.5) * (ux * ux + uy * uy);
+    const C om = co.om, om1 = co.om1;
+    // omega * w_q * rho and omega * w_q * drho per weight class
+    const C R0 = (om * C(4.0 / 9.0)) * rho, Ra = (om * C(1.0 / 9.0)) * rho, Rd = (om * C(1.0 / 36.0)) * rho;
+    const C E0 = (om * C(4.0 / 9.0)) * drho, Ea = (om * C(1.0 / 9.0)) * drho, Ed = (om * C(1.0 / 36.0)) * drho;
+    C uF = C(0), K0 = C(0), Ka = C(0), Kd = C(0);
+    if (HAS_F) {
+        uF = ux * Fx + uy * Fy;
+        K0 = co.kk * C(4.0 / 9.0);
+        Ka = co.kk * C(1.0 / 9.0);
+        Kd = co.kk * C(1.0 / 36.0);
+    }
+    // rest
+    {
+        C G = E0 - R0 * usq;
+        if (HAS_F) G = G + K0 * (C(-3) * uF);
+        f[0] = om1 * f[0] + G;
+    }
+#define LBM_PAIR(I, J, T, CF, RQ, EQ, KQ)                                     \
+    {                                                                         \
+        const C t = (T);                                                      \
+        C P = EQ + RQ * (C(4.5) * (t * t) - usq);                             \
+        C Q = (C(3) * RQ) * t;                                                \
+        if (HAS_F) {                                                          \
+            const C cf = (CF);                                                \
+            P = P + KQ * (C(9) * (t * cf) - C(3) * uF);                       \
+            Q = Q + (C(3) * KQ) * cf;                                         \
+        }                                                                     \
+        f[I] = om1 * f[I] + (P + Q);                                          \
+        f[J] = om1 * f[J] + (P - Q);                                          \
+    }
+    LBM_PAIR(1, 3, ux, Fx, Ra, Ea, Ka)
+    LBM_PAIR(2, 4, uy, Fy, Ra, Ea, Ka)
+    LBM_PAIR(5, 7, ux + uy, Fx + Fy, Rd, Ed, Kd)
+    LBM_PAIR(6, 8, uy - ux, Fy - Fx, Rd, Ed, Kd)
+#undef LBM_PAIR
+}
+
+// Discrete adjoint of one node's collision (see the oracle's derivation):
+// from lam = dL/d(post-collision f) gives g = dL/df' and dL/dF.
+template <class C, bool HAS_F>
+__device__ __forceinline__ void adjoint_node(const C f[9], const C lam[9], C Fx, C Fy, C omega,
+                                             C g[9], C &dFx, C &dFy) {
+    C drho, rho, inv, ux, uy;
+    moments<C, HAS_F>(f, Fx, Fy, drho, rho, inv, ux, uy);
+    const C usq = C(1.5) * (ux * ux + uy * uy);
+    const C kk = C(1) - C(0.5) * omega;
+    C Vx = C(0), Vy = C(0), a = C(0), gx = C(0), gy = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const C w = wgt<C>(i);
+        const C t = C(cx(i)) * ux + C(cy(i)) * uy;
+        const C l = lam[i];
+        a += l * (w * (C(1) + C(3) * t + C(4.5) * t * t - usq));
+        const C wr = omega * w * rho;
+        C dx = wr * (C(3 * cx(i)) + C(9) * t * C(cx(i)) - C(3) * ux);
+        C dy = wr * (C(3 * cy(i)) + C(9) * t * C(cy(i)) - C(3) * uy);
+        if (HAS_F) {
+            const C cf = C(cx(i)) * Fx + C(cy(i)) * Fy;
+            dx += kk * w * (C(-3) * Fx + C(9) * cf * C(cx(i)));
+            dy += kk * w * (C(-3) * Fy + C(9) * cf * C(cy(i)));
+        }
+        Vx += l * dx;
+        Vy += l * dy;
+        gx += l * (kk * w * (C(3) * (C(cx(i)) - ux) + C(9) * t * C(cx(i))));
+        gy += l * (kk * w * (C(3) * (C(cy(i)) - uy) + C(9) * t * C(cy(i))));
+    }
+    a *= omega;
+#pragma unroll
+    for (int j = 0; j < 9; ++j)
+        g[j] = (C(1) - omega) * lam[j] + a + ((C(cx(j)) - ux) * Vx + (C(cy(j)) - uy) * Vy) * inv;
+    dFx = C(0.5) * Vx * inv + gx;
+    dFy = C(0.5) * Vy * inv + gy;
+}
+
+// ------------------------------------------------------------- step kernel
+
+// Gather of the aligned vectors (and the one edge value per x-shifted slot)
+// that hold f'_i of this thread's VEC nodes.  Slot pulled for link i: i
+// (two-lattice) or opp(i) (AA gather/scatter step); AA local step reads the
+// thread's own vectors.
+template <class S, int MODE, class A>
+__device__ __forceinline__ void gather_raw(const A &ad, const typename S::R *src, bool active, int lane,
+                                           V16<typename S::R, S::VEC> raw[9], typename S::R edge[9]) {
+    typedef typename S::R R;
+    constexpr int VEC = S::VEC;
+    constexpr bool NC = (MODE == MODE_TWO_LATTICE);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int slot = (MODE == MODE_AA_PULLPUSH) ? opp(i) : i;
+        const int dy = (MODE == MODE_AA_LOCAL) ? 0 : -cy(i);
+        if (active) raw[i] = ld16<NC, R, VEC>(src + ad.vidx(slot, dy));
+        else raw[i].u = make_uint4(0, 0, 0, 0);
+        edge[i] = R(0);
+    }
+    if constexpr (MODE == MODE_AA_LOCAL) return;
+    // A lane whose VEC nodes are all solid moves no vectors, but for the
+    // diagonal links its neighbour lane pulls one value through it from the
+    // row above or below, which may be fluid: load just that value.
+    if (!active && ad.valid) {
+#pragma unroll
+        for (int i = 5; i < 9; ++i) {
+            const int slot = (MODE == MODE_AA_PULLPUSH) ? opp(i) : i;
+            if (cx(i) == 1 && ad.right_in_warp(lane))
+                raw[i].v[VEC - 1] = ld1<NC>(src + ad.eidx(slot, VEC - 1, 0, -cy(i)));
+            if (cx(i) == -1 && ad.left_in_warp(lane))
+                raw[i].v[0] = ld1<NC>(src + ad.eidx(slot, 0, 0, -cy(i)));
+        }
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int slot = (MODE == MODE_AA_PULLPUSH) ? opp(i) : i;
+        if (cx(i) == 1 && active && !ad.left_in_warp(lane))
+            edge[i] = ld1<NC>(src + ad.eidx(slot, 0, -1, -cy(i)));
+        if (cx(i) == -1 && active && !ad.right_in_warp(lane))
+            edge[i] = ld1<NC>(src + ad.eidx(slot, VEC - 1, 1, -cy(i)));
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (cx(i) == 1) {
+            const R l = shfl_up1(raw[i].v[VEC - 1]);
+            if (ad.left_in_warp(lane)) edge[i] = l;
+        } else if (cx(i) == -1) {
+            const R r = shfl_down1(raw[i].v[0]);
+            if (ad.right_in_warp(lane)) edge[i] = r;
+        }
+    }
+}
+
+// Stored value of link i for node k of the thread (before bounce-back).
+template <class S, int I, int K>
+__device__ __forceinline__ typename S::R pulled(const V16<typename S::R, S::VEC> raw[9],
+                                                const typename S::R edge[9], int mode) {
+    constexpr int VEC = S::VEC;
+    if (mode == MODE_AA_LOCAL || cx(I) == 0) return raw[I].v[K];
+    if (cx(I) == 1) return K == 0 ? edge[I] : raw[I].v[(K + VEC - 1) % VEC];
+    return K == VEC - 1 ? edge[I] : raw[I].v[(K + 1) % VEC];
+}
+
+template <class S, int K, int MODE>
+__device__ __forceinline__ void node_values(const V16<typename S::R, S::VEC> raw[9],
+                                            const typename S::R edge[9], typename S::C f[9]) {
+    f[0] = S::dec(pulled<S, 0, K>(raw, edge, MODE));
+    f[1] = S::dec(pulled<S, 1, K>(raw, edge, MODE));
+    f[2] = S::dec(pulled<S, 2, K>(raw, edge, MODE));
+    f[3] = S::dec(pulled<S, 3, K>(raw, edge, MODE));
+    f[4] = S::dec(pulled<S, 4, K>(raw, edge, MODE));
+    f[5] = S::dec(pulled<S, 5, K>(raw, edge, MODE));
+    f[6] = S::dec(pulled<S, 6, K>(raw, edge, MODE));
+    f[7] = S::dec(pulled<S, 7, K>(raw, edge, MODE));
+    f[8] = S::dec(pulled<S, 8, K>(raw, edge, MODE));
+}
+
+// Half-way bounce-back for the links of node k whose mask bit is set:
+// f'_i = (stored post-collision value of link opp(i) at x) + wall term.
+template <class S, int MODE, class A>
+__device__ __forceinline__ void bounce(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
+                                       int k, unsigned m, typename S::C f[9]) {
+    typedef typename S::C C;
+    constexpr bool NC = (MODE == MODE_TWO_LATTICE);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (m & (1u << (i - 1))) {
+            C v;
+            if (MODE == MODE_TWO_LATTICE) v = S::dec(ld1<NC>(src + ad.eidx(opp(i), k, 0, 0)));
+            else if (MODE == MODE_AA_PULLPUSH) v = S::dec(ld1<NC>(src + ad.eidx(i, k, 0, 0)));
+            else v = f[i];
+            if (ph.has_wall) v = v + C(ph.wt[wall_side(g, ad.gx(k), ad.gy(), i)][i]);
+            f[i] = v;
+        }
+    }
+}
+
+template <class S, int FORCE, class A>
+__device__ __forceinline__ void load_force(const Geo &g, const Phys &ph, const A &ad, bool active,
+                                           typename S::C Fx[S::VEC], typename S::C Fy[S::VEC]) {
+    typedef typename S::C C;
+    constexpr int VEC = S::VEC;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        Fx[k] = C(ph.fx);
+        Fy[k] = C(ph.fy);
+    }
+    if (FORCE == FORCE_FIELD && active && ad.in_domain()) {
+        const C *F = reinterpret_cast<const C *>(ph.force);
+        const long long n = ad.node(0);
+        constexpr int CH = VEC * (int)sizeof(C) / 16; // 16-byte chunks
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            V16<C, 16 / sizeof(C)> a = ld16<true, C, 16 / sizeof(C)>(F + n + c * (16 / sizeof(C)));
+            V16<C, 16 / sizeof(C)> b = ld16<true, C, 16 / sizeof(C)>(F + g.nnode + n + c * (16 / sizeof(C)));
+#pragma unroll
+            for (int j = 0; j < (int)(16 / sizeof(C)); ++j) {
+                Fx[c * (16 / sizeof(C)) + j] = a.v[j];
+                Fy[c * (16 / sizeof(C)) + j] = b.v[j];
+            }
+        }
+    }
+}
+
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE, int K>
+__device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad, const typename St<P>::R *src,
+                                        unsigned long long mv, const V16<typename St<P>::R, St<P>::VEC> raw[9],
+                                        const typename St<P>::R edge[9], const typename St<P>::C Fx[],
+                                        const typename St<P>::C Fy[], const Coef<typename St<P>::C> &co,
+                                        V16<typename St<P>::R, St<P>::VEC> out[9]) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    C f[9];
+    node_values<S, K, MODE>(raw, edge, f);
+    const unsigned m = HAS_MASK ? (unsigned)((mv >> (8 * K)) & 0xFFu) : 0u;
+    if (HAS_MASK && m == 0xFFu) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(C(0));
+        return;
+    }
+    if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, src, K, m, f);
+    collide<C, FORCE != FORCE_NONE>(f, Fx[K], Fy[K], co);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);
+}
+
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE, int K>
+struct NodeLoop {
+    static __device__ __forceinline__ void run(const Geo &g, const Phys &ph, const A &ad,
+                                               const typename St<P>::R *src, unsigned long long mv,
+                                               const V16<typename St<P>::R, St<P>::VEC> raw[9],
+                                               const typename St<P>::R edge[9], const typename St<P>::C Fx[],
+                                               const typename St<P>::C Fy[], const Coef<typename St<P>::C> &co,
+                                               V16<typename St<P>::R, St<P>::VEC> out[9]) {
+        NodeLoop<P, A, MODE, HAS_MASK, FORCE, K - 1>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+        do_node<P, A, MODE, HAS_MASK, FORCE, K - 1>(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+    }
+};
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
+struct NodeLoop<P, A, MODE, HAS_MASK, FORCE, 0> {
+    static __device__ __forceinline__ void run(const Geo &, const Phys &, const A &, const typename St<P>::R *,
+                                               unsigned long long, const V16<typename St<P>::R, St<P>::VEC> *,
+                                               const typename St<P>::R *, const typename St<P>::C *,
+                                               const typename St<P>::C *, const Coef<typename St<P>::C> &,
+                                               V16<typename St<P>::R, St<P>::VEC> *) {}
+};
+
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
+__global__ void __launch_bounds__(STEP_BLOCK) k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v) {
+    typedef St<P> S;
+    typedef typename S::R R;
+    typedef typename S::C C;
+    constexpr int VEC = S::VEC;
+    const R *src = reinterpret_cast<const R *>(src_v);
+    R *dst = reinterpret_cast<R *>(dst_v);
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const A ad(g, gtid);
+    const int lane = threadIdx.x & 31;
+
+    unsigned long long mv = 0;
+    if (HAS_MASK) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
+    const bool active = ad.valid && !(HAS_MASK && mv == mask_ones<VEC>());
+    if (!__any_sync(LBM_FULL, active)) return; // whole warp solid: no traffic
+
+    V16<R, VEC> raw[9];
+    R edge[9];
+    gather_raw<S, MODE>(ad, src, active, lane, raw, edge);
+
+    C Fx[VEC], Fy[VEC];
+    load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
+    const Coef<C> co(ph);
+
+    V16<R, VEC> out[9];
+    NodeLoop<P, A, MODE, HAS_MASK, FORCE, VEC>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+    if (!active) return;
+
+    if (MODE == MODE_TWO_LATTICE) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st16<R, VEC>(dst + ad.vidx(i, 0), out[i]);
+    } else if (MODE == MODE_AA_LOCAL) {
+        // post-collision value of link i goes to slot opp(i) of the same node
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st16<R, VEC>(dst + ad.vidx(opp(i), 0), out[i]);
+    } else {
+        // AA gather/scatter step: f''_i(x) goes to slot i at x + c_i, or to
+        // slot opp(i) at x when x + c_i is solid or beyond a wall (link
+        // opp(i) of x bounces).  Each target slot has exactly one writer.
+        st16<R, VEC>(dst + ad.vidx(0, 0), out[0]);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const unsigned long long rep = mask_rep<VEC>(opp(i) - 1);
+            if (cx(i) == 0 && (!HAS_MASK || (mv & rep) == 0ull)) {
+                st16<R, VEC>(dst + ad.vidx(i, cy(i)), out[i]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    const unsigned m = HAS_MASK ? (unsigned)((mv >> (8 * k)) & 0xFFu) : 0u;
+                    if (m == 0xFFu) continue;
+                    if (m & (1u << (opp(i) - 1)))
+                        dst[ad.eidx(opp(i), k, 0, 0)] = out[i].v[k];
+                    else
+                        dst[ad.eidx(i, k, cx(i), cy(i))] = out[i].v[k];
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- adjoint kernel
+
+// One adjoint step on the dense two-lattice layout: re-gathers f' from the
+// stored state A_t, reads lam_in = dL/dA_{t+1} at the node, and pushes
+// g_j = dL/df'_j back along each link (to slot j at x - c_j, or to slot
+// opp(j) at x for a bounced link): the transpose of the pull gather.  Every
+// target has one writer; solid nodes write 0 to their own slots.
+template <int P, int FORCE>
+__global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys ph, const void *state_v,
+                                                        const void *lam_in_v, void *lam_out_v, void *gF_v) {
+    typedef St<P> S;
+    typedef typename S::R R;
+    typedef typename S::C C;
+    constexpr int VEC = S::VEC;
+    constexpr int LC = 16 / (int)sizeof(C); // compute values per 16 bytes
+    constexpr int CH = VEC / LC;            // 16-byte chunks per thread per slot
+    const R *src = reinterpret_cast<const R *>(state_v);
+    const C *lin = reinterpret_cast<const C *>(lam_in_v);
+    C *lout = reinterpret_cast<C *>(lam_out_v);
+    C *gF = reinterpret_cast<C *>(gF_v);
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const DenseAddr<VEC> ad(g, gtid);
+    const int lane = threadIdx.x & 31;
+    unsigned long long mv = 0;
+    if (g.has_mask) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
+    const bool active = ad.valid;
+    if (!__any_sync(LBM_FULL, active)) return;
+
+    V16<R, VEC> raw[9];
+    R edge[9];
+    gather_raw<S, MODE_TWO_LATTICE>(ad, src, active, lane, raw, edge);
+    C Fx[VEC], Fy[VEC];
+    load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
+    const C omega = C(ph.omega);
+    const long long n0 = ad.node(0);
+
+    C gout[9][VEC];
+    C dFx[VEC], dFy[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        dFx[k] = C(0);
+        dFy[k] = C(0);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) gout[j][k] = C(0);
+    }
+    C lam[9][VEC];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            V16<C, LC> v;
+            if (active) v = ld16<true, C, LC>(lin + j * g.nnode + n0 + c * LC);
+            else v.u = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int q = 0; q < LC; ++q) lam[j][c * LC + q] = v.v[q];
+        }
+    }
+#define LBM_ADJ_NODE(K)                                                                   \
+    if constexpr ((K) < VEC) {                                                            \
+        const unsigned m = (unsigned)((mv >> (8 * (K))) & 0xFFu);                         \
+        if (m != 0xFFu) {                                                                 \
+            C f[9];                                                                       \
+            node_values<S, ((K) < VEC ? (K) : 0), MODE_TWO_LATTICE>(raw, edge, f);        \
+            if (m != 0u) bounce<S, MODE_TWO_LATTICE>(g, ph, ad, src, (K), m, f);          \
+            C l[9], gg[9];                                                                \
+            for (int j = 0; j < 9; ++j) l[j] = lam[j][(K)];                               \
+            adjoint_node<C, FORCE != FORCE_NONE>(f, l, Fx[(K)], Fy[(K)], omega, gg,       \
+                                                 dFx[(K)], dFy[(K)]);                     \
+            for (int j = 0; j < 9; ++j) gout[j][(K)] = gg[j];                             \
+        }                                                                                 \
+    }
+    LBM_ADJ_NODE(0)
+    LBM_ADJ_NODE(1)
+    LBM_ADJ_NODE(2)
+    LBM_ADJ_NODE(3)
+    LBM_ADJ_NODE(4)
+    LBM_ADJ_NODE(5)
+    LBM_ADJ_NODE(6)
+    LBM_ADJ_NODE(7)
+#undef LBM_ADJ_NODE
+    if (!active) return;
+
+    // push
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const unsigned long long rep = j == 0 ? 0ull : mask_rep<VEC>(j - 1);
+        if (cx(j) == 0 && (j == 0 || (mv & rep) == 0ull)) {
+            // all VEC targets are the aligned vector at (x0, y - c_y)
+            const long long base = j * g.nnode + (long long)ad.row(-cy(j)) * g.nx + ad.x0;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                V16<C, LC> v;
+#pragma unroll
+                for (int q = 0; q < LC; ++q) v.v[q] = gout[j][c * LC + q];
+                st16<C, LC>(lout + base + c * LC, v);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                const unsigned m = (unsigned)((mv >> (8 * k)) & 0xFFu);
+                long long dst;
+                if (m == 0xFFu) dst = j * g.nnode + n0 + k;                  // solid: own slot, 0
+                else if (j > 0 && (m & (1u << (j - 1)))) dst = opp(j) * g.nnode + n0 + k; // bounced
+                else dst = ad.eidx(j, k, -cx(j), -cy(j));
+                lout[dst] = gout[j][k];
+            }
+        }
+    }
+    // dL/dF accumulation (fluid nodes contribute, solid nodes add 0)
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        V16<C, LC> a = ld16<false, C, LC>(gF + n0 + c * LC);
+        V16<C, LC> b = ld16<false, C, LC>(gF + g.nnode + n0 + c * LC);
+#pragma unroll
+        for (int q = 0; q < LC; ++q) {
+            a.v[q] += dFx[c * LC + q];
+            b.v[q] += dFy[c * LC + q];
+        }
+        st16<C, LC>(gF + n0 + c * LC, a);
+        st16<C, LC>(gF + g.nnode + n0 + c * LC, b);
+    }
+}
+
+// ------------------------------------------------------------- per-node helpers
+
+// Index of slot j at in-domain node (x, y), both layouts.
+__device__ __forceinline__ long long cidx(const Geo &g, int x, int y, int j) {
+    if (g.layout == LBM_DENSE) return j * g.nslot + (long long)y * g.nx + x;
+    const int t = __ldg(g.tile_id + (y >> 4) * g.ntx + (x >> 4));
+    return ((long long)t * 9 + j) * TILE_N + (y & 15) * TILE + (x & 15);
+}
+__device__ __forceinline__ unsigned node_mask(const Geo &g, int x, int y) {
+    if (g.layout == LBM_DENSE) return g.has_mask ? __ldg(g.mask + (long long)y * g.nx + x) : 0u;
+    const int t = __ldg(g.tile_id + (y >> 4) * g.ntx + (x >> 4));
+    return t < 0 ? 0xFFu : __ldg(g.mask + (long long)t * TILE_N + (y & 15) * TILE + (x & 15));
+}
+__device__ __forceinline__ void wrap_xy(const Geo &g, int &x, int &y) {
+    if (x < 0) x += g.nx; else if (x >= g.nx) x -= g.nx;
+    if (y < 0) y += g.ny; else if (y >= g.ny) y -= g.ny;
+}
+
+// Canonical A_i(x, y) (shifted) in each phase of the lattice.
+template <class S>
+__device__ __forceinline__ typename S::C canon_read(const Geo &g, int phase, const typename S::R *M, int x,
+                                                    int y, int i, unsigned m) {
+    if (phase == PH_PLAIN) return S::dec(M[cidx(g, x, y, i)]);
+    if (phase == PH_SWAPPED) return S::dec(M[cidx(g, x, y, opp(i))]);
+    if (i == 0) return S::dec(M[cidx(g, x, y, 0)]);
+    if (m & (1u << (opp(i) - 1))) return S::dec(M[cidx(g, x, y, opp(i))]);
+    int x2 = x + cx(i), y2 = y + cy(i);
+    wrap_xy(g, x2, y2);
+    return S::dec(M[cidx(g, x2, y2, i)]);
+}
+template <class S>
+__device__ __forceinline__ void canon_write(const Geo &g, int phase, typename S::R *M, int x, int y, int i,
+                                            typename S::C v) {
+    M[cidx(g, x, y, phase == PH_SWAPPED ? opp(i) : i)] = S::enc(v);
+}
+
+// Gathered f'_i(x, y) of the next step (shifted), in each phase.
+template <class S>
+__device__ __forceinline__ void gather_node(const Geo &g, const Phys &ph, int phase, const typename S::R *M,
+                                            int x, int y, unsigned m, typename S::C f[9]) {
+    typedef typename S::C C;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const bool b = i > 0 && (m & (1u << (i - 1)));
+        C v;
+        if (phase == PH_STREAMED) {
+            v = S::dec(M[cidx(g, x, y, i)]);
+        } else if (b) {
+            v = S::dec(M[cidx(g, x, y, phase == PH_PLAIN ? opp(i) : i)]);
+        } else {
+            int sx = x - cx(i), sy = y - cy(i);
+            wrap_xy(g, sx, sy);
+            v = S::dec(M[cidx(g, sx, sy, phase == PH_PLAIN ? i : opp(i))]);
+        }
+        if (b && ph.has_wall) v = v + C(ph.wt[wall_side(g, x, y, i)][i]);
+        f[i] = v;
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void node_force(const Geo &g, const Phys &ph, long long n, C &Fx, C &Fy) {
+    if (ph.force_mode == FORCE_FIELD) {
+        const C *F = reinterpret_cast<const C *>(ph.force);
+        Fx = F[n];
+        Fy = F[g.nnode + n];
+    } else {
+        Fx = C(ph.fx);
+        Fy = C(ph.fy);
+    }
+}
+
+#define LBM_NODE_LOOP(g)                                                                   \
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;                  \
+    if (n >= (long long)(g).nx * (g).ny) return;                                           \
+    const int y = (int)(n / (g).nx), x = (int)(n - (long long)y * (g).nx);
+
+template <int P>
+__global__ void k_init(const Geo g, int phase, const void *rho_v, const void *u_v, void *lat_v) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    LBM_NODE_LOOP(g)
+    const unsigned m = node_mask(g, x, y);
+    if (m == 0xFFu && g.layout != LBM_DENSE) {
+        // node in an absent tile has no storage
+        const int t = __ldg(g.tile_id + (y >> 4) * g.ntx + (x >> 4));
+        if (t < 0) return;
+    }
+    typename S::R *M = reinterpret_cast<typename S::R *>(lat_v);
+    const C *rho = reinterpret_cast<const C *>(rho_v);
+    const C *u = reinterpret_cast<const C *>(u_v);
+    C drho = C(0), ux = C(0), uy = C(0);
+    if (m != 0xFFu) {
+        if (rho) drho = rho[n] - C(1);
+        if (u) {
+            ux = u[n];
+            uy = u[g.nnode + n];
+        }
+    }
+    const C r = C(1) + drho;
+    const C usq = C(1.5) * (ux * ux + uy * uy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const C t = C(cx(i)) * ux + C(cy(i)) * uy;
+        const C v = (m == 0xFFu) ? C(0) : wgt<C>(i) * (drho + r * (C(3) * t + C(4.5) * t * t - usq));
+        canon_write<S>(g, phase, M, x, y, i, v);
+    }
+}
+
+template <int P>
+__global__ void k_set_f(const Geo g, int phase, const void *f_v, void *lat_v) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    LBM_NODE_LOOP(g)
+    const unsigned m = node_mask(g, x, y);
+    if (g.layout != LBM_DENSE && __ldg(g.tile_id + (y >> 4) * g.ntx + (x >> 4)) < 0) return;
+    const C *f = reinterpret_cast<const C *>(f_v);
+    typename S::R *M = reinterpret_cast<typename S::R *>(lat_v);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const C v = (m == 0xFFu) ? C(0) : f[i * g.nnode + n] - wgt<C>(i);
+        canon_write<S>(g, phase, M, x, y, i, v);
+    }
+}
+
+template <int P>
+__global__ void k_get_f(const Geo g, int phase, const void *lat_v, void *f_v) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    LBM_NODE_LOOP(g)
+    const unsigned m = node_mask(g, x, y);
+    const typename S::R *M = reinterpret_cast<const typename S::R *>(lat_v);
+    C *f = reinterpret_cast<C *>(f_v);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const C v = (m == 0xFFu) ? C(0) : canon_read<S>(g, phase, M, x, y, i, m);
+        f[i * g.nnode + n] = wgt<C>(i) + v;
+    }
+}
+
+template <int P>
+__global__ void k_macros(const Geo g, const Phys ph, int phase, const void *lat_v, void *rho_v, void *u_v) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    LBM_NODE_LOOP(g)
+    const unsigned m = node_mask(g, x, y);
+    C r = C(1), ux = C(0), uy = C(0);
+    if (m != 0xFFu) {
+        C f[9];
+        gather_node<S>(g, ph, phase, reinterpret_cast<const typename S::R *>(lat_v), x, y, m, f);
+        C Fx, Fy, drho, inv;
+        node_force<C>(g, ph, n, Fx, Fy);
+        moments<C, true>(f, Fx, Fy, drho, r, inv, ux, uy);
+    }
+    if (rho_v) reinterpret_cast<C *>(rho_v)[n] = r;
+    if (u_v) {
+        reinterpret_cast<C *>(u_v)[n] = ux;
+        reinterpret_cast<C *>(u_v)[g.nnode + n] = uy;
+    }
+}
+
+// FP64 block reduction of 4 values; thread 0 returns the sums.
+__device__ __forceinline__ void block_sum4(double v[4], double *out) {
+    __shared__ double sm[4][AUX_BLOCK / 32];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(LBM_FULL, v[c], o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sm[c][w] = v[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < AUX_BLOCK / 32; ++k) s += sm[c][k];
+            out[c] = s;
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(AUX_BLOCK) k_reduce(const Geo g, const Phys ph, int phase, int kind,
+                                                      const void *lat_v, const void *target_v, double *partial) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    const typename S::R *M = reinterpret_cast<const typename S::R *>(lat_v);
+    const C *tgt = reinterpret_cast<const C *>(target_v);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const long long N = (long long)g.nx * g.ny;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(n / g.nx), x = (int)(n - (long long)y * g.nx);
+        const unsigned m = node_mask(g, x, y);
+        if (m == 0xFFu) continue;
+        if (kind == 0) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double v = (double)canon_read<S>(g, phase, M, x, y, i, m);
+                acc[0] += v;
+                acc[1] += cx(i) * v;
+                acc[2] += cy(i) * v;
+            }
+        } else {
+            C f[9];
+            gather_node<S>(g, ph, phase, M, x, y, m, f);
+            C Fx, Fy, drho, r, inv, ux, uy;
+            node_force<C>(g, ph, n, Fx, Fy);
+            moments<C, true>(f, Fx, Fy, drho, r, inv, ux, uy);
+            if (kind == 1) {
+                const double dx = (double)ux - (double)tgt[n], dy = (double)uy - (double)tgt[g.nnode + n];
+                acc[0] += dx * dx + dy * dy;
+            } else {
+                acc[0] += 0.5 * (double)r * ((double)ux * (double)ux + (double)uy * (double)uy);
+            }
+        }
+    }
+    block_sum4(acc, partial + 4 * blockIdx.x);
+}
+
+template <int P>
+__global__ void __launch_bounds__(AUX_BLOCK) k_reduce_final(const double *partial, int nparts, double *out) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += partial[4 * p + c];
+    block_sum4(acc, out);
+}
+
+// Transpose of the macros at the current (two-lattice, dense) state.
+template <int P>
+__global__ void k_macros_adjoint(const Geo g, const Phys ph, const void *state_v, const void *grho_v,
+                                 const void *gu_v, void *lam_v, void *gF_v) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    LBM_NODE_LOOP(g)
+    const unsigned m = node_mask(g, x, y);
+    C *lam = reinterpret_cast<C *>(lam_v);
+    if (m == 0xFFu) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) lam[j * g.nnode + n] = C(0);
+        return;
+    }
+    C f[9];
+    gather_node<S>(g, ph, PH_PLAIN, reinterpret_cast<const typename S::R *>(state_v), x, y, m, f);
+    C Fx, Fy, drho, r, inv, ux, uy;
+    node_force<C>(g, ph, n, Fx, Fy);
+    moments<C, true>(f, Fx, Fy, drho, r, inv, ux, uy);
+    const C gr = grho_v ? reinterpret_cast<const C *>(grho_v)[n] : C(0);
+    const C gx = gu_v ? reinterpret_cast<const C *>(gu_v)[n] : C(0);
+    const C gy = gu_v ? reinterpret_cast<const C *>(gu_v)[g.nnode + n] : C(0);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const C v = gr + ((C(cx(j)) - ux) * gx + (C(cy(j)) - uy) * gy) * inv;
+        if (j > 0 && (m & (1u << (j - 1)))) {
+            lam[opp(j) * g.nnode + n] = v;
+        } else {
+            int sx = x - cx(j), sy = y - cy(j);
+            wrap_xy(g, sx, sy);
+            lam[j * g.nnode + (long long)sy * g.nx + sx] = v;
+        }
+    }
+    if (gF_v) {
+        C *gF = reinterpret_cast<C *>(gF_v);
+        gF[n] += C(0.5) * gx * inv;
+        gF[g.nnode + n] += C(0.5) * gy * inv;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+template <int P, class A, int MODE, bool HM, int F>
+static cudaError_t step_launch(const Geo &g, const Phys &ph, long long nthreads, const void *src, void *dst,
+                               cudaStream_t s) {
+    if (nthreads <= 0) return cudaSuccess;
+    const long long blocks = (nthreads + STEP_BLOCK - 1) / STEP_BLOCK;
+    k_step<P, A, MODE, HM, F><<<(unsigned)blocks, STEP_BLOCK, 0, s>>>(g, ph, src, dst);
+    return cudaGetLastError();
+}
+template <int P, class A, int MODE, bool HM>
+static cudaError_t step_force(const Geo &g, const Phys &ph, long long n, const void *src, void *dst,
+                              cudaStream_t s) {
+    switch (ph.force_mode) {
+    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, n, src, dst, s);
+    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, n, src, dst, s);
+    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, n, src, dst, s);
+    }
+}
+template <int P, class A, bool HM>
+static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, long long n, const void *src, void *dst,
+                             cudaStream_t s) {
+    switch (mode) {
+    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, n, src, dst, s);
+    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, n, src, dst, s);
+    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, n, src, dst, s);
+    }
+}
+
+template <int P>
+cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, cudaStream_t s) {
+    constexpr int VEC = St<P>::VEC;
+    if (g.layout == LBM_DENSE) {
+        const long long n = (long long)g.ny * (g.nx / VEC);
+        if (g.has_mask) return step_mode<P, DenseAddr<VEC>, true>(g, ph, mode, n, src, dst, s);
+        return step_mode<P, DenseAddr<VEC>, false>(g, ph, mode, n, src, dst, s);
+    }
+    const long long n = (long long)g.ntiles * TileAddr<VEC>::TPT;
+    return step_mode<P, TileAddr<VEC>, true>(g, ph, mode, n, src, dst, s);
+}
+
+static inline unsigned node_blocks(const Geo &g) {
+    return (unsigned)(((long long)g.nx * g.ny + AUX_BLOCK - 1) / AUX_BLOCK);
+}
+
+template <int P>
+cudaError_t launch_init(const Geo &g, int phase, const void *rho, const void *u, void *lat, cudaStream_t s) {
+    k_init<P><<<node_blocks(g), AUX_BLOCK, 0, s>>>(g, phase, rho, u, lat);
+    return cudaGetLastError();
+}
+template <int P>
+cudaError_t launch_set_f(const Geo &g, int phase, const void *f, void *lat, cudaStream_t s) {
+    k_set_f<P><<<node_blocks(g), AUX_BLOCK, 0, s>>>(g, phase, f, lat);
+    return cudaGetLastError();
+}
+template <int P>
+cudaError_t launch_get_f(const Geo &g, int phase, const void *lat, void *f, cudaStream_t s) {
+    k_get_f<P><<<node_blocks(g), AUX_BLOCK, 0, s>>>(g, phase, lat, f);
+    return cudaGetLastError();
+}
+template <int P>
+cudaError_t launch_macros(const Geo &g, const Phys &ph, int phase, const void *lat, void *rho, void *u,
+                          cudaStream_t s) {
+    k_macros<P><<<node_blocks(g), AUX_BLOCK, 0, s>>>(g, ph, phase, lat, rho, u);
+    return cudaGetLastError();
+}
+template <int P>
+cudaError_t launch_reduce(const Geo &g, const Phys &ph, int phase, int kind, const void *lat, const void *target,
+                          double *partial, double *out, cudaStream_t s) {
+    k_reduce<P><<<RED_BLOCKS, AUX_BLOCK, 0, s>>>(g, ph, phase, kind, lat, target, partial);
+    k_reduce_final<P><<<1, AUX_BLOCK, 0, s>>>(partial, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+template <int P>
+cudaError_t launch_adjoint(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
+                           void *grad_force, cudaStream_t s) {
+    constexpr int VEC = St<P>::VEC;
+    const long long n = (long long)g.ny * (g.nx / VEC);
+    const unsigned blocks = (unsigned)((n + STEP_BLOCK - 1) / STEP_BLOCK);
+    if (n == 0) return cudaSuccess;
+    switch (ph.force_mode) {
+    case FORCE_NONE:
+        k_adjoint<P, FORCE_NONE><<<blocks, STEP_BLOCK, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force);
+        break;
+    case FORCE_UNIFORM:
+        k_adjoint<P, FORCE_UNIFORM><<<blocks, STEP_BLOCK, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force);
+        break;
+    default:
+        k_adjoint<P, FORCE_FIELD><<<blocks, STEP_BLOCK, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force);
+    }
+    return cudaGetLastError();
+}
+template <int P>
+cudaError_t launch_macros_adjoint(const Geo &g, const Phys &ph, const void *state, const void *g_rho,
+                                  const void *g_u, void *lam, void *grad_force, cudaStream_t s) {
+    k_macros_adjoint<P><<<node_blocks(g), AUX_BLOCK, 0, s>>>(g, ph, state, g_rho, g_u, lam, grad_force);
+    return cudaGetLastError();
+}
+
+#define LBM_INSTANTIATE(P)                                                                                  \
+    template cudaError_t launch_step<P>(const Geo &, const Phys &, int, const void *, void *, cudaStream_t); \
+    template cudaError_t launch_init<P>(const Geo &, int, const void *, const void *, void *, cudaStream_t); \
+    template cudaError_t launch_set_f<P>(const Geo &, int, const void *, void *, cudaStream_t);             \
+    template cudaError_t launch_get_f<P>(const Geo &, int, const void *, void *, cudaStream_t);             \
+    template cudaError_t launch_macros<P>(const Geo &, const Phys &, int, const void *, void *, void *,    \
+                                          cudaStream_t);                                                    \
+    template cudaError_t launch_reduce<P>(const Geo &, const Phys &, int, int, const void *, const void *, \
+                                          double *, double *, cudaStream_t);                                \
+    template cudaError_t launch_adjoint<P>(const Geo &, const Phys &, const void *, const void *, void *,  \
+                                           void *, cudaStream_t);                                           \
+    template cudaError_t launch_macros_adjoint<P>(const Geo &, const Phys &, const void *, const void *,   \
+                                                  const void *, void *, void *, cudaStream_t);
+
+} // namespace lbm

@@ -1,0 +1,144 @@
+"""GPU adjoint: lbm_backward / lbm_macros_backward behind LBMFunction against
+the FP64 oracle's adjoint chain, finite differences of the GPU's own FP64
+forward, and the checkpointed vs un-checkpointed schedule."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2108_13241_gb300 import inputs
+from tests import cases as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2108_13241_gb300 import build
+    build.build()
+    from paper_2108_13241_gb300 import autograd, lbm
+    return lbm, autograd
+
+
+def channel_case(nx=48, ny=32, count=3, seed=inputs.GEOMETRY_SEED):
+    solid, _ = inputs.channel_cylinders(nx, ny, count=count, rmin=3, rmax=5, clearance=2, seed=seed)
+    c = C.Case("chan%dx%d" % (nx, ny), nx, ny, 0.8, px=True, py=False, walls={"north": (0.01, 0.0)}, solid=solid)
+    c.rho0 = 1.0 + 0.01 * inputs.random_field((ny, nx), 91)
+    c.u0 = 0.02 * inputs.random_field((2, ny, nx), 92)
+    c.force_field = 1e-4 * inputs.random_field((2, ny, nx), 93)
+    return c
+
+
+def oracle_grads(orc, c, T, ut):
+    s = C.oracle_setup(orc, c)
+    mask, _ = orc.link_mask(s, c.solid)
+    A0 = orc.init_equilibrium(s, mask, c.rho0, c.u0)
+    states = [A0]
+    for _ in range(T):
+        states.append(orc.step(s, mask, states[-1], c.force_field))
+    fl = mask != 0xFF
+    _, u = orc.macros(s, mask, states[-1], force=c.force_field)
+    g_u = 2.0 * (u - ut) * fl / fl.sum()
+    gF = np.zeros_like(c.force_field)
+    lam = orc.macros_adjoint(s, mask, states[-1], None, g_u, force=c.force_field, grad_force=gF)
+    for t in range(T - 1, -1, -1):
+        lam = orc.adjoint_step(s, mask, states[t], lam, force=c.force_field, grad_force=gF)
+    return A0, lam, gF, mask, orc.loss_mse(u, ut, mask)
+
+
+def gpu_grads(L, c, T, K, ut, precision, A0):
+    lbm, ag = L
+    sim = lbm.LBM(precision=precision, **C.gpu_kwargs(c))
+    dt = sim.dtype
+    f0 = torch.as_tensor(A0, dtype=dt, device="cuda").requires_grad_(True)
+    F = torch.as_tensor(c.force_field, dtype=dt, device="cuda").requires_grad_(True)
+    rho, u = ag.simulate(sim, T, f0, F, K=K)
+    fl = torch.as_tensor(sim.link_mask() != 0xFF, device="cuda")
+    target = torch.as_tensor(ut, dtype=dt, device="cuda")
+    loss = (((u - target) ** 2).sum(0) * fl).sum() / fl.sum()
+    loss.backward()
+    return f0.grad.double().cpu().numpy(), F.grad.double().cpu().numpy(), float(loss), sim
+
+
+@pytest.mark.parametrize("T,K", [(1, 1), (30, 7), (24, 24)])
+def test_adjoint_fp64_matches_oracle_chain(L, orc, T, K):
+    c = channel_case()
+    ut = inputs.target_velocity(c.nx, c.ny, c.solid, amp=0.02)
+    A0, lam, gF, mask, loss = oracle_grads(orc, c, T, ut)
+    g0, gFg, lg, _ = gpu_grads(L, c, T, K, ut, "f64", A0)
+    fl = mask != 0xFF
+    assert abs(lg - loss) <= 1e-12 * abs(loss)
+    assert C.rel_l2(g0, lam, fl) <= 1e-10
+    assert C.rel_l2(gFg, gF, fl) <= 1e-10
+    assert np.all(g0[:, ~fl] == 0)
+
+
+def test_adjoint_fp32_matches_oracle_chain(L, orc):
+    c = channel_case()
+    T = 40
+    ut = inputs.target_velocity(c.nx, c.ny, c.solid, amp=0.02)
+    A0, lam, gF, mask, loss = oracle_grads(orc, c, T, ut)
+    g0, gFg, lg, _ = gpu_grads(L, c, T, 7, ut, "f32", A0)
+    fl = mask != 0xFF
+    assert C.rel_l2(gFg, gF, fl) <= 1e-4
+    assert C.rel_l2(g0, lam, fl) <= 1e-4
+
+
+def test_checkpointed_equals_unsegmented_bitwise(L):
+    c = channel_case()
+    ut = inputs.target_velocity(c.nx, c.ny, c.solid, amp=0.02)
+    A0 = None
+    from oracle import oracle as orc
+    s = C.oracle_setup(orc, c)
+    mask, _ = orc.link_mask(s, c.solid)
+    A0 = orc.init_equilibrium(s, mask, c.rho0, c.u0)
+    a = gpu_grads(L, c, 50, 7, ut, "f32", A0)
+    b = gpu_grads(L, c, 50, 50, ut, "f32", A0)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_force_gradient_matches_fp64_finite_differences_full_size(L):
+    """Channel 512 x 256, 12 cylinders (r 6..12), tau 0.8, F = (1e-5, 0) per
+    node, T = 2000, checkpoint every 45, loss = mean |u_T - u*|^2: the FP32
+    adjoint's dL/dF against central differences of the FP64 GPU forward on 64
+    seeded entries, within 1e-4 relative."""
+    lbm, ag = L
+    nx, ny, T, K = 512, 256, 2000, 45
+    solid, _ = inputs.channel_cylinders(nx, ny, count=12, rmin=6, rmax=12, clearance=2)
+    F = np.zeros((2, ny, nx))
+    F[0] = 1e-5
+    F[:, solid.astype(bool)] = 0
+    ut = inputs.target_velocity(nx, ny, solid, amp=0.02)
+    kw = dict(nx=nx, ny=ny, tau=0.8, solid=solid, periodic_y=False)
+    sim32 = lbm.LBM(precision="f32", **kw)
+    Ft = torch.as_tensor(F, dtype=torch.float32, device="cuda").requires_grad_(True)
+    rho, u = ag.simulate(sim32, T, None, Ft, K=K)
+    fl = torch.as_tensor(solid == 0, device="cuda")
+    loss = (((u - torch.as_tensor(ut, dtype=torch.float32, device="cuda")) ** 2).sum(0) * fl).sum() / fl.sum()
+    loss.backward()
+    g = Ft.grad.double().cpu().numpy()
+
+    sim64 = lbm.LBM(precision="f64", **kw)
+    target = torch.as_tensor(ut, dtype=torch.float64, device="cuda")
+
+    def loss64(Fa):
+        sim64.init_equilibrium(None, None)
+        sim64.set_force(Fa)
+        sim64.step(T)
+        return sim64.loss_mse(target)
+
+    rng = inputs.SplitMix64(inputs.FD_SEED)
+    fluid = np.argwhere(solid == 0)
+    gmax = np.abs(g).max()
+    worst = 0.0
+    for _ in range(64):
+        y, x = fluid[rng.next_u64() % len(fluid)]
+        comp = int(rng.next_u64() % 2)
+        h = 1e-7
+        Fp = torch.as_tensor(F, dtype=torch.float64, device="cuda")
+        Fm = Fp.clone()
+        Fp[comp, y, x] += h
+        Fm[comp, y, x] -= h
+        fd = (loss64(Fp) - loss64(Fm)) / (2 * h)
+        err = abs(fd - g[comp, y, x]) / max(abs(fd), 1e-3 * gmax)
+        worst = max(worst, err)
+    assert worst <= 1e-4, worst

@@ -1,0 +1,97 @@
+"""Host-side checks of the CUDA library that need no GPU: the shared library
+builds, loads and exports every function include/lbm.h declares; parameter
+validation; the host-built link mask and tile tables match the oracle bit for
+bit."""
+import numpy as np
+import pytest
+
+from paper_2108_13241_gb300 import inputs
+from tests.cases import SIDES
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2108_13241_gb300 import build
+    build.build()
+    from paper_2108_13241_gb300 import lbm as L
+    return L
+
+
+def test_library_exports_every_declared_symbol(lbm):
+    L = lbm._load()
+    syms = lbm.header_symbols()
+    assert len(syms) >= 20
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert missing == []
+
+
+def test_status_strings(lbm):
+    for s in range(7):
+        assert lbm.lbm_status_string(s)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=24), dict(nx=0), dict(ny=0), dict(tau=0.5), dict(tau=float("nan")),
+    dict(periodic_mismatch=True), dict(sparse_periodic_ny=True),
+])
+def test_invalid_parameters_rejected(lbm, bad):
+    nx, ny, tau = bad.get("nx", 32), bad.get("ny", 16), bad.get("tau", 0.8)
+    p, _ = lbm.make_params(nx, ny, tau, stream=0)
+    if bad.get("periodic_mismatch"):
+        p.east.periodic = 0
+    if bad.get("sparse_periodic_ny"):
+        p.ny = 20
+        p.layout = lbm.LBM_SPARSE_TILE16
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_workspace_bytes(p)
+    assert e.value.status == lbm.LBM_ERR_INVALID
+
+
+def test_workspace_bytes_counts_lattices(lbm):
+    for prec, s in (("f64", 8), ("f32", 4), ("f16s", 2)):
+        for pat, nl in (("two_lattice", 2), ("aa", 1)):
+            p, _ = lbm.make_params(64, 48, 0.8, precision=prec, pattern=pat, stream=0)
+            b = lbm.lbm_workspace_bytes(p)
+            lat = 9 * 64 * 48 * s
+            assert nl * lat <= b <= nl * lat + 64 * 1024
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (48, 32), (37, 48), (20, 64)])
+@pytest.mark.parametrize("px,py", [(1, 1), (1, 0), (0, 1), (0, 0)])
+def test_geometry_tables_match_oracle(lbm, orc, shape, px, py):
+    ny, nx = shape
+    sparse_ok = not (py and ny % 16)
+    for frac, seed in [(0.0, 1), (0.3, 2), (0.9, 3)]:
+        solid = inputs.random_solid(nx, ny, frac, seed=seed + nx * ny)
+        solid[: min(16, ny), :16] = 1
+        s = orc.Setup(nx=nx, ny=ny, tau=0.8, periodic_x=bool(px), periodic_y=bool(py))
+        omask, onf = orc.link_mask(s, solid)
+        layout = "sparse" if sparse_ok else "dense"
+        p, keep = lbm.make_params(nx, ny, 0.8, solid=solid, periodic_x=bool(px), periodic_y=bool(py),
+                                  layout=layout, stream=0)
+        mask, tid, nbr, nf = lbm.lbm_geometry(p)
+        assert np.array_equal(mask, omask)
+        assert nf == onf
+        if sparse_ok:
+            otid, onbr = orc.tile_map(s, omask)
+            assert np.array_equal(tid, otid)
+            assert np.array_equal(nbr, onbr)
+
+
+def test_geometry_porous_generator_tables(lbm, orc):
+    solid, phi, nd = inputs.porous_discs(256, 128, 0.5, rmin=8, rmax=32, seed=inputs.GEOMETRY_SEED)
+    assert abs(phi - 0.5) < 0.05 and nd > 5
+    s = orc.Setup(nx=256, ny=128, tau=0.8, periodic_x=True, periodic_y=False)
+    omask, onf = orc.link_mask(s, solid)
+    otid, onbr = orc.tile_map(s, omask)
+    p, keep = lbm.make_params(256, 128, 0.8, solid=solid, periodic_y=False, layout="sparse", stream=0)
+    mask, tid, nbr, nf = lbm.lbm_geometry(p)
+    assert np.array_equal(mask, omask) and nf == onf
+    assert np.array_equal(tid, otid) and np.array_equal(nbr, onbr)
+
+
+def test_sides_order_matches_header(lbm):
+    p, _ = lbm.make_params(32, 16, 0.8, periodic_x=False, periodic_y=False,
+                           walls={"west": (1, 2), "east": (3, 4), "south": (5, 6), "north": (7, 8)}, stream=0)
+    got = [(getattr(p, s).ux, getattr(p, s).uy) for s in SIDES]
+    assert got == [(1, 2), (3, 4), (5, 6), (7, 8)]
