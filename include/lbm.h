@@ -4,9 +4,9 @@
  * The library implements the fused pull stream-and-collide update of
  * Tomczak, "Data-Oriented Language Implementation of Lattice-Boltzmann Method
  * for Dense and Sparse Geometries" (arXiv 2108.13241), Algorithm 1, with the
- * BGK operator (Eq. Omega^BGK, Eq. omega, Eq. f^eq), the moments of
- * Eq. (rho, v), half-way bounce-back walls and obstacles (Sec. 3, boundary
- * paragraph), dense and 16x16-tiled sparse storage (Sec. 4.2.1, "tile" and
+ * BGK operator (Eq. 4, Eq. 5, Eq. 6), the moments of
+ * Eq. 2, half-way bounce-back walls and obstacles (Sec. 3, boundary
+ * paragraph), dense and 16x16-tiled sparse storage (Sec. 4.2.2, "tile" and
  * "pointer tile" layouts), plus a Guo body force, an in-place AA pattern,
  * FP64 / FP32 / FP16-shifted storage and a hand-written adjoint.
  *
@@ -84,7 +84,7 @@ typedef struct {
                                  fluid; read during lbm_workspace_bytes and
                                  lbm_create only                           */
     double tau;               /* BGK relaxation time > 0.5; omega = 1/tau,
-                                 nu = (tau - 1/2)/3 (Eq. omega)            */
+                                 nu = (tau - 1/2)/3 (Eq. 5)            */
     double fx, fy;            /* uniform body-force density (Guo forcing)  */
     lbm_side west, east, south, north;
     lbm_precision precision;
@@ -116,18 +116,18 @@ lbm_status lbm_destroy(lbm_ctx *ctx);
  * The pointer is kept, not copied. */
 lbm_status lbm_set_force(lbm_ctx *ctx, const void *d_force);
 
-/* Algorithm 1, initialisation: A_i = f^eq_i(rho, u) (Eq. f^eq) at fluid
+/* Algorithm 1, initialisation: A_i = f^eq_i(rho, u) (Eq. 6) at fluid
  * nodes.  d_rho [ny][nx] and d_u [2][ny][nx] in compute type; NULL means
  * rho = 1 / u = 0.  Resets the step counter and the AA phase. */
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *d_rho, const void *d_u);
 
 /* n time steps of Algorithm 1 (n >= 0): per fluid node, pull gather with
- * bounce-back, moments (Eq. rho, v, u shifted by F/2), f^eq (Eq. f^eq), BGK
- * relaxation (Eq. LBM, Eq. Omega^BGK) plus the Guo source
+ * bounce-back, moments (Eq. 2, u shifted by F/2), f^eq (Eq. 6), BGK
+ * relaxation (Eq. 3, Eq. 4) plus the Guo source
  * (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F, aligned store. */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
 
-/* Density and velocity of the current state (Eq. rho, v on the gathered f'
+/* Density and velocity of the current state (Eq. 2 on the gathered f'
  * of the next step, u = (m + F/2)/rho).  d_rho [ny][nx], d_u [2][ny][nx]
  * (compute type); either may be NULL.  Solid nodes give rho = 1, u = 0. */
 lbm_status lbm_macros(lbm_ctx *ctx, void *d_rho, void *d_u);

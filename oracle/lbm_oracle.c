@@ -17,7 +17,7 @@
  *   orc_init_equilibrium Algorithm 1, initialisation (f = f^eq(rho, v));
  *   orc_step / orc_run   Algorithm 1, one/many fused pull steps + swap
  *                        (body in step_body.inc);
- *   orc_macros           Eq. (rho, v) on the gathered f', F/2 shift of the
+ *   orc_macros           Eq. 2 on the gathered f', F/2 shift of the
  *                        Guo forcing;
  *   orc_adjoint_step     discrete adjoint (transpose of the linearisation) of
  *                        orc_step;
@@ -135,7 +135,7 @@ int orc_tile_map(const orc_params *p, const uint8_t *mask, int32_t *tile_id,
     return 0;
 }
 
-/* Algorithm 1, initialisation: A_i = f^eq_i(rho, u) (Eq. f^eq) at fluid
+/* Algorithm 1, initialisation: A_i = f^eq_i(rho, u) (Eq. 6) at fluid
  * nodes; solid nodes hold w_i.  NULL fields mean rho = 1, u = 0. */
 void orc_init_equilibrium(const orc_params *p, const uint8_t *mask,
                           const double *rho, const double *ux, const double *uy,
@@ -191,7 +191,7 @@ static void orc_gather(const orc_params *p, const uint8_t *mask, const double *A
     }
 }
 
-/* Eq. (rho, v) applied to the gathered f' of the next step, with the F/2
+/* Eq. 2 applied to the gathered f' of the next step, with the F/2
  * velocity shift of the Guo forcing.  Solid nodes report rho = 1, u = 0. */
 void orc_macros(const orc_params *p, const uint8_t *mask, const double *force,
                 const double *A, double *rho, double *ux, double *uy)

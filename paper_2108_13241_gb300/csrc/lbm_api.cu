@@ -246,6 +246,16 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
             ph.wt[s][i] = sides[s]->periodic ? 0.0 : 6.0 * W[i] * (CX[i] * sides[s]->ux + CY[i] * sides[s]->uy);
             if (ph.wt[s][i] != 0.0) ph.has_wall = 1;
         }
+    // FP32 constants from the rounded omega in FP32 arithmetic, so that
+    // om1_f + omega_f == 1 exactly (1 - omega is exact for omega in (0, 2)):
+    // otherwise BGK would scale mass and momentum by (om1 + omega) each step.
+    ph.omega_f = (float)ph.omega;
+    ph.om1_f = 1.0f - ph.omega_f;
+    ph.kk_f = 1.0f - 0.5f * ph.omega_f;
+    ph.fx_f = (float)ph.fx;
+    ph.fy_f = (float)ph.fy;
+    for (int s = 0; s < WALL_SIDES; ++s)
+        for (int i = 0; i < 9; ++i) ph.wt_f[s][i] = (float)ph.wt[s][i];
     set_force_mode(c);
 
     lbm_status st = LBM_OK;

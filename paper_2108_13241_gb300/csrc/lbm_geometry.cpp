@@ -3,7 +3,7 @@
 //
 // Sec. 3 (boundary paragraph) stores a node-type field with a bitmask of the
 // neighbours that are present; here one byte per node holds which of the 8
-// moving links bounce back (half-way bounce-back).  Sec. 4.2.1 stores only the
+// moving links bounce back (half-way bounce-back).  Sec. 4.2.2 stores only the
 // 16^2-node tiles that hold data ("pointer tile"); here the kept tiles are
 // numbered densely and a table of 9 neighbour-tile numbers replaces pointers.
 #include <vector>

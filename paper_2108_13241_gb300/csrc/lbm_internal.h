@@ -56,6 +56,9 @@ struct Phys {
     int force_mode;
     int has_wall;          // some wall term is nonzero
     double wt[WALL_SIDES][9];
+    // the same constants rounded to FP32 on the host (FP32 / FP16s kernels)
+    float omega_f, om1_f, kk_f, fx_f, fy_f;
+    float wt_f[WALL_SIDES][9];
 };
 
 // Launchers, defined in lbm_kernels.cuh and instantiated per precision P

@@ -3,12 +3,12 @@
 // per-precision translation units kern_f64.cu, kern_f32.cu, kern_f16s.cu.
 //
 // The hot kernel (k_step) is Algorithm 1's fused pull kernel (Sec. 3):
-// gather f'_i = A_i(x - c_i) with half-way bounce-back, moments (Eq. rho, v),
-// equilibrium (Eq. f^eq), BGK relaxation (Eq. LBM, Eq. Omega^BGK) with a Guo
+// gather f'_i = A_i(x - c_i) with half-way bounce-back, moments (Eq. 2),
+// equilibrium (Eq. 6), BGK relaxation (Eq. 3, Eq. 4) with a Guo
 // body-force source, aligned store.  Design for GB300:
-//  * SoA slots, one 16-byte vector per thread and slot: VEC = 2 (FP64),
-//    4 (FP32) or 8 (FP16-shifted) consecutive nodes along x;
-//  * the x-shifted pulls (c_x != 0, the uncoalesced loads Sec. 4.2.1
+//  * SoA slots, one vector per thread and slot: 16 bytes = 2 FP64 or 4 FP32
+//    nodes, 8 bytes = 4 FP16 nodes, consecutive along x;
+//  * the x-shifted pulls (c_x != 0, the uncoalesced loads Sec. 4.2.2
 //    reports) take the aligned vector and one value from the neighbouring
 //    lane (__shfl_up/down_sync); only lanes at a warp or row edge load that
 //    value from memory (an L1/L2 hit);
@@ -65,23 +65,30 @@ template <> struct St<LBM_F32> {
 template <> struct St<LBM_F16S> {
     typedef unsigned short R; // binary16 bits of f_i - w_i
     typedef float C;
-    enum { VEC = 8 };
+    enum { VEC = 4 };          // 8-byte vectors: 4 nodes per thread
     static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)); }
     static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c)); }
 };
 
+// One aligned vector of VEC stored values: 16 bytes (FP64, FP32) or 8 bytes
+// (FP16s), moved with one load or store instruction.
+template <int BYTES> struct VecWord;
+template <> struct VecWord<16> { typedef uint4 T; static __device__ __forceinline__ uint4 zero() { return make_uint4(0, 0, 0, 0); } };
+template <> struct VecWord<8> { typedef uint2 T; static __device__ __forceinline__ uint2 zero() { return make_uint2(0, 0); } };
+
 template <class R, int VEC> union V16 {
-    uint4 u;
+    typename VecWord<(int)sizeof(R) * VEC>::T u;
     R v[VEC];
 };
 
 template <bool NC, class R, int VEC>
 __device__ __forceinline__ V16<R, VEC> ld16(const R *p) {
+    typedef typename VecWord<(int)sizeof(R) * VEC>::T W;
     V16<R, VEC> r;
     if (NC)
-        r.u = __ldg(reinterpret_cast<const uint4 *>(p));
+        r.u = __ldg(reinterpret_cast<const W *>(p));
     else
-        r.u = *reinterpret_cast<const uint4 *>(p);
+        r.u = *reinterpret_cast<const W *>(p);
     return r;
 }
 template <bool NC, class R> __device__ __forceinline__ R ld1(const R *p) {
@@ -92,7 +99,10 @@ template <> __device__ __forceinline__ unsigned short ld1<true, unsigned short>(
     return __ldg(p);
 }
 template <class R, int VEC> __device__ __forceinline__ void st16(R *p, const V16<R, VEC> &v) {
-    *reinterpret_cast<uint4 *>(p) = v.u;
+    *reinterpret_cast<typename VecWord<(int)sizeof(R) * VEC>::T *>(p) = v.u;
+}
+template <class R, int VEC> __device__ __forceinline__ void zero16(V16<R, VEC> &v) {
+    v.u = VecWord<(int)sizeof(R) * VEC>::zero();
 }
 
 __device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(LBM_FULL, v, 1); }
@@ -136,7 +146,8 @@ template <int VEC> struct DenseAddr {
     long long nslot;
     const uint8_t *mask;
 
-    __device__ __forceinline__ DenseAddr(const Geo &g, long long gtid) {
+    // 2-D launch: (vector column, row) = (blockIdx.x * blockDim.x + tid, row)
+    __device__ __forceinline__ DenseAddr(const Geo &g, int col, int row_) {
         nx = g.nx;
         ny = g.ny;
         px = g.periodic_x;
@@ -144,11 +155,9 @@ template <int VEC> struct DenseAddr {
         nslot = g.nslot;
         mask = g.mask;
         nvx = nx / VEC;
-        const long long nvec = (long long)ny * nvx;
-        valid = gtid < nvec;
-        const long long v = valid ? gtid : nvec - 1;
-        y = (int)(v / nvx);
-        xv = (int)(v - (long long)y * nvx);
+        valid = col < nvx;
+        xv = valid ? col : nvx - 1;
+        y = row_;
         x0 = xv * VEC;
     }
     __device__ __forceinline__ int row(int dy) const {
@@ -188,15 +197,16 @@ template <int VEC> struct TileAddr {
     int nb[9];
     const uint8_t *mask;
 
-    __device__ __forceinline__ TileAddr(const Geo &g, long long gtid) {
+    // 1-D launch over tiles (TPT threads per tile); the row argument is unused
+    __device__ __forceinline__ TileAddr(const Geo &g, int gtid, int) {
         nx = g.nx;
         ny = g.ny;
         mask = g.mask;
-        long long tt = gtid / TPT;
+        int tt = gtid / TPT;
         valid = tt < g.ntiles;
         if (!valid) tt = g.ntiles - 1;
-        t = (int)tt;
-        const int tl = (int)(gtid - (gtid / TPT) * TPT);
+        t = tt;
+        const int tl = gtid - (gtid / TPT) * TPT;
         ly = tl / TPR;
         xv = tl - ly * TPR;
         lx0 = xv * VEC;
@@ -246,7 +256,31 @@ __device__ __forceinline__ int wall_side(const Geo &g, int x, int y, int i) {
 
 // ------------------------------------------------------------- physics
 
-// Moments of the gathered shifted f' (Eq. rho, v; u shifted by F/2).
+// Physics constants in the compute type (FP32 copies are rounded on the host,
+// so no kernel converts FP64 to FP32).
+template <class C> struct PC;
+template <> struct PC<double> {
+    static __device__ __forceinline__ double omega(const Phys &p) { return p.omega; }
+    static __device__ __forceinline__ double om1(const Phys &p) { return 1.0 - p.omega; }
+    static __device__ __forceinline__ double kk(const Phys &p) { return 1.0 - 0.5 * p.omega; }
+    static __device__ __forceinline__ double fx(const Phys &p) { return p.fx; }
+    static __device__ __forceinline__ double fy(const Phys &p) { return p.fy; }
+    static __device__ __forceinline__ double wt(const Phys &p, int s, int i) { return p.wt[s][i]; }
+};
+template <> struct PC<float> {
+    static __device__ __forceinline__ float omega(const Phys &p) { return p.omega_f; }
+    static __device__ __forceinline__ float om1(const Phys &p) { return p.om1_f; }
+    static __device__ __forceinline__ float kk(const Phys &p) { return p.kk_f; }
+    static __device__ __forceinline__ float fx(const Phys &p) { return p.fx_f; }
+    static __device__ __forceinline__ float fy(const Phys &p) { return p.fy_f; }
+    static __device__ __forceinline__ float wt(const Phys &p, int s, int i) { return p.wt_f[s][i]; }
+};
+
+// Correctly rounded reciprocal (same value as 1/x in IEEE division).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
+// Moments of the gathered shifted f' (Eq. 2; u shifted by F/2).
 template <class C, bool HAS_F>
 __device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rho, C &inv, C &ux,
                                         C &uy) {
@@ -254,7 +288,7 @@ __device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rh
     rho = C(1) + drho;
     const C mx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const C my = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
-    inv = C(1) / rho;
+    inv = recip(rho);
     if (HAS_F) {
         ux = (mx + C(0.5) * Fx) * inv;
         uy = (my + C(0.5) * Fy) * inv;
@@ -267,7 +301,7 @@ __device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rh
 template <class C> struct Coef {
     C om, om1, kk;
     __device__ __forceinline__ explicit Coef(const Phys &ph)
-        : om(C(ph.omega)), om1(C(1) - C(ph.omega)), kk(C(1) - C(0.5) * C(ph.omega)) {}
+        : om(PC<C>::omega(ph)), om1(PC<C>::om1(ph)), kk(PC<C>::kk(ph)) {}
 };
 
 // BGK relaxation with Guo source, in shifted variables, in place on f:
@@ -370,7 +404,7 @@ __device__ __forceinline__ void gather_raw(const A &ad, const typename S::R *src
         const int slot = (MODE == MODE_AA_PULLPUSH) ? opp(i) : i;
         const int dy = (MODE == MODE_AA_LOCAL) ? 0 : -cy(i);
         if (active) raw[i] = ld16<NC, R, VEC>(src + ad.vidx(slot, dy));
-        else raw[i].u = make_uint4(0, 0, 0, 0);
+        else zero16(raw[i]);
         edge[i] = R(0);
     }
     if constexpr (MODE == MODE_AA_LOCAL) return;
@@ -445,7 +479,7 @@ __device__ __forceinline__ void bounce(const Geo &g, const Phys &ph, const A &ad
             if (MODE == MODE_TWO_LATTICE) v = S::dec(ld1<NC>(src + ad.eidx(opp(i), k, 0, 0)));
             else if (MODE == MODE_AA_PULLPUSH) v = S::dec(ld1<NC>(src + ad.eidx(i, k, 0, 0)));
             else v = f[i];
-            if (ph.has_wall) v = v + C(ph.wt[wall_side(g, ad.gx(k), ad.gy(), i)][i]);
+            if (ph.has_wall) v = v + PC<C>::wt(ph, wall_side(g, ad.gx(k), ad.gy(), i), i);
             f[i] = v;
         }
     }
@@ -458,8 +492,8 @@ __device__ __forceinline__ void load_force(const Geo &g, const Phys &ph, const A
     constexpr int VEC = S::VEC;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-        Fx[k] = C(ph.fx);
-        Fy[k] = C(ph.fy);
+        Fx[k] = PC<C>::fx(ph);
+        Fy[k] = PC<C>::fy(ph);
     }
     if (FORCE == FORCE_FIELD && active && ad.in_domain()) {
         const C *F = reinterpret_cast<const C *>(ph.force);
@@ -500,60 +534,32 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
     for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);
 }
 
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE, int K>
-struct NodeLoop {
+// Nodes K0 .. K1-1 of the thread, in order (compile-time unrolled).
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE, int K, int K1>
+struct NodeRange {
     static __device__ __forceinline__ void run(const Geo &g, const Phys &ph, const A &ad,
                                                const typename St<P>::R *src, unsigned long long mv,
                                                const V16<typename St<P>::R, St<P>::VEC> raw[9],
                                                const typename St<P>::R edge[9], const typename St<P>::C Fx[],
                                                const typename St<P>::C Fy[], const Coef<typename St<P>::C> &co,
                                                V16<typename St<P>::R, St<P>::VEC> out[9]) {
-        NodeLoop<P, A, MODE, HAS_MASK, FORCE, K - 1>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
-        do_node<P, A, MODE, HAS_MASK, FORCE, K - 1>(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+        if constexpr (K < K1) {
+            do_node<P, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+            NodeRange<P, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+        }
     }
 };
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
-struct NodeLoop<P, A, MODE, HAS_MASK, FORCE, 0> {
-    static __device__ __forceinline__ void run(const Geo &, const Phys &, const A &, const typename St<P>::R *,
-                                               unsigned long long, const V16<typename St<P>::R, St<P>::VEC> *,
-                                               const typename St<P>::R *, const typename St<P>::C *,
-                                               const typename St<P>::C *, const Coef<typename St<P>::C> &,
-                                               V16<typename St<P>::R, St<P>::VEC> *) {}
-};
 
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
-__global__ void __launch_bounds__(STEP_BLOCK) k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v) {
-    typedef St<P> S;
-    typedef typename S::R R;
-    typedef typename S::C C;
-    constexpr int VEC = S::VEC;
-    const R *src = reinterpret_cast<const R *>(src_v);
-    R *dst = reinterpret_cast<R *>(dst_v);
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const A ad(g, gtid);
-    const int lane = threadIdx.x & 31;
-
-    unsigned long long mv = 0;
-    if (HAS_MASK) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
-    const bool active = ad.valid && !(HAS_MASK && mv == mask_ones<VEC>());
-    if (!__any_sync(LBM_FULL, active)) return; // whole warp solid: no traffic
-
-    V16<R, VEC> raw[9];
-    R edge[9];
-    gather_raw<S, MODE>(ad, src, active, lane, raw, edge);
-
-    C Fx[VEC], Fy[VEC];
-    load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
-    const Coef<C> co(ph);
-
-    V16<R, VEC> out[9];
-    NodeLoop<P, A, MODE, HAS_MASK, FORCE, VEC>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
-    if (!active) return;
-
-    if (MODE == MODE_TWO_LATTICE) {
+// Stores of the thread's VEC nodes for the three step kinds.
+template <int P, class A, int MODE, bool HAS_MASK>
+__device__ __forceinline__ void store_all(const A &ad, typename St<P>::R *dst, unsigned long long mv,
+                                           const V16<typename St<P>::R, St<P>::VEC> out[9]) {
+    typedef typename St<P>::R R;
+    constexpr int VEC = St<P>::VEC;
+    if constexpr (MODE == MODE_TWO_LATTICE) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) st16<R, VEC>(dst + ad.vidx(i, 0), out[i]);
-    } else if (MODE == MODE_AA_LOCAL) {
+    } else if constexpr (MODE == MODE_AA_LOCAL) {
         // post-collision value of link i goes to slot opp(i) of the same node
 #pragma unroll
         for (int i = 0; i < 9; ++i) st16<R, VEC>(dst + ad.vidx(opp(i), 0), out[i]);
@@ -582,6 +588,37 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_step(const Geo g, const Phys ph,
     }
 }
 
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
+__global__ void __launch_bounds__(STEP_BLOCK) k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v,
+                                                     int y0) {
+    typedef St<P> S;
+    typedef typename S::R R;
+    typedef typename S::C C;
+    constexpr int VEC = S::VEC;
+    const R *src = reinterpret_cast<const R *>(src_v);
+    R *dst = reinterpret_cast<R *>(dst_v);
+    const A ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + (int)blockIdx.y);
+    const int lane = threadIdx.x & 31;
+
+    unsigned long long mv = 0;
+    if (HAS_MASK) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
+    const bool active = ad.valid && !(HAS_MASK && mv == mask_ones<VEC>());
+    if (!__any_sync(LBM_FULL, active)) return; // whole warp solid: no traffic
+
+    V16<R, VEC> raw[9];
+    R edge[9];
+    gather_raw<S, MODE>(ad, src, active, lane, raw, edge);
+    if (!active) return; // no collective operation follows
+
+    C Fx[VEC], Fy[VEC];
+    load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
+    const Coef<C> co(ph);
+
+    V16<R, VEC> out[9];
+    NodeRange<P, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+    store_all<P, A, MODE, HAS_MASK>(ad, dst, mv, out);
+}
+
 // ------------------------------------------------------------- adjoint kernel
 
 // One adjoint step on the dense two-lattice layout: re-gathers f' from the
@@ -591,7 +628,8 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_step(const Geo g, const Phys ph,
 // target has one writer; solid nodes write 0 to their own slots.
 template <int P, int FORCE>
 __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys ph, const void *state_v,
-                                                        const void *lam_in_v, void *lam_out_v, void *gF_v) {
+                                                        const void *lam_in_v, void *lam_out_v, void *gF_v,
+                                                        int y0) {
     typedef St<P> S;
     typedef typename S::R R;
     typedef typename S::C C;
@@ -602,8 +640,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
     const C *lin = reinterpret_cast<const C *>(lam_in_v);
     C *lout = reinterpret_cast<C *>(lam_out_v);
     C *gF = reinterpret_cast<C *>(gF_v);
-    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const DenseAddr<VEC> ad(g, gtid);
+    const DenseAddr<VEC> ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + (int)blockIdx.y);
     const int lane = threadIdx.x & 31;
     unsigned long long mv = 0;
     if (g.has_mask) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
@@ -615,7 +652,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
     gather_raw<S, MODE_TWO_LATTICE>(ad, src, active, lane, raw, edge);
     C Fx[VEC], Fy[VEC];
     load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
-    const C omega = C(ph.omega);
+    const C omega = PC<C>::omega(ph);
     const long long n0 = ad.node(0);
 
     C gout[9][VEC];
@@ -759,7 +796,7 @@ __device__ __forceinline__ void gather_node(const Geo &g, const Phys &ph, int ph
             wrap_xy(g, sx, sy);
             v = S::dec(M[cidx(g, sx, sy, phase == PH_PLAIN ? i : opp(i))]);
         }
-        if (b && ph.has_wall) v = v + C(ph.wt[wall_side(g, x, y, i)][i]);
+        if (b && ph.has_wall) v = v + PC<C>::wt(ph, wall_side(g, x, y, i), i);
         f[i] = v;
     }
 }
@@ -771,8 +808,8 @@ __device__ __forceinline__ void node_force(const Geo &g, const Phys &ph, long lo
         Fx = F[n];
         Fy = F[g.nnode + n];
     } else {
-        Fx = C(ph.fx);
-        Fy = C(ph.fy);
+        Fx = PC<C>::fx(ph);
+        Fy = PC<C>::fy(ph);
     }
 }
 
@@ -976,30 +1013,55 @@ __global__ void k_macros_adjoint(const Geo g, const Phys ph, const void *state_v
 
 // ------------------------------------------------------------- launchers
 
+// Launch shape.  Dense: blockIdx.y = row (in chunks of at most 65535 rows),
+// blockIdx.x * blockDim.x + tid = vector column, blockDim.x = the row's vector
+// count rounded up to a warp, at most STEP_BLOCK.  Tiled: 1-D over tiles.
+struct Shape {
+    unsigned bx, gx, rows;
+    bool dense;
+};
+template <int VEC> static Shape step_shape(const Geo &g) {
+    Shape sh;
+    sh.dense = g.layout == LBM_DENSE;
+    if (sh.dense) {
+        const int nvx = g.nx / VEC;
+        sh.bx = (unsigned)(((nvx + 31) / 32) * 32);
+        if (sh.bx > (unsigned)STEP_BLOCK) sh.bx = STEP_BLOCK;
+        sh.gx = (unsigned)((nvx + sh.bx - 1) / sh.bx);
+        sh.rows = (unsigned)g.ny;
+    } else {
+        const long long n = (long long)g.ntiles * TileAddr<VEC>::TPT;
+        sh.bx = STEP_BLOCK;
+        sh.gx = (unsigned)((n + STEP_BLOCK - 1) / STEP_BLOCK);
+        sh.rows = 1;
+    }
+    return sh;
+}
+
 template <int P, class A, int MODE, bool HM, int F>
-static cudaError_t step_launch(const Geo &g, const Phys &ph, long long nthreads, const void *src, void *dst,
-                               cudaStream_t s) {
-    if (nthreads <= 0) return cudaSuccess;
-    const long long blocks = (nthreads + STEP_BLOCK - 1) / STEP_BLOCK;
-    k_step<P, A, MODE, HM, F><<<(unsigned)blocks, STEP_BLOCK, 0, s>>>(g, ph, src, dst);
+static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, cudaStream_t s) {
+    const Shape sh = step_shape<St<P>::VEC>(g);
+    if (sh.gx == 0) return cudaSuccess;
+    for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
+        const unsigned gy = sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u;
+        k_step<P, A, MODE, HM, F><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, (int)y0);
+    }
     return cudaGetLastError();
 }
 template <int P, class A, int MODE, bool HM>
-static cudaError_t step_force(const Geo &g, const Phys &ph, long long n, const void *src, void *dst,
-                              cudaStream_t s) {
+static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, cudaStream_t s) {
     switch (ph.force_mode) {
-    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, n, src, dst, s);
-    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, n, src, dst, s);
-    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, n, src, dst, s);
+    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, src, dst, s);
+    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, s);
+    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, src, dst, s);
     }
 }
 template <int P, class A, bool HM>
-static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, long long n, const void *src, void *dst,
-                             cudaStream_t s) {
+static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, cudaStream_t s) {
     switch (mode) {
-    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, n, src, dst, s);
-    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, n, src, dst, s);
-    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, n, src, dst, s);
+    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, src, dst, s);
+    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, s);
+    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, src, dst, s);
     }
 }
 
@@ -1007,12 +1069,10 @@ template <int P>
 cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, cudaStream_t s) {
     constexpr int VEC = St<P>::VEC;
     if (g.layout == LBM_DENSE) {
-        const long long n = (long long)g.ny * (g.nx / VEC);
-        if (g.has_mask) return step_mode<P, DenseAddr<VEC>, true>(g, ph, mode, n, src, dst, s);
-        return step_mode<P, DenseAddr<VEC>, false>(g, ph, mode, n, src, dst, s);
+        if (g.has_mask) return step_mode<P, DenseAddr<VEC>, true>(g, ph, mode, src, dst, s);
+        return step_mode<P, DenseAddr<VEC>, false>(g, ph, mode, src, dst, s);
     }
-    const long long n = (long long)g.ntiles * TileAddr<VEC>::TPT;
-    return step_mode<P, TileAddr<VEC>, true>(g, ph, mode, n, src, dst, s);
+    return step_mode<P, TileAddr<VEC>, true>(g, ph, mode, src, dst, s);
 }
 
 static inline unsigned node_blocks(const Geo &g) {
@@ -1050,19 +1110,20 @@ cudaError_t launch_reduce(const Geo &g, const Phys &ph, int phase, int kind, con
 template <int P>
 cudaError_t launch_adjoint(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
                            void *grad_force, cudaStream_t s) {
-    constexpr int VEC = St<P>::VEC;
-    const long long n = (long long)g.ny * (g.nx / VEC);
-    const unsigned blocks = (unsigned)((n + STEP_BLOCK - 1) / STEP_BLOCK);
-    if (n == 0) return cudaSuccess;
-    switch (ph.force_mode) {
-    case FORCE_NONE:
-        k_adjoint<P, FORCE_NONE><<<blocks, STEP_BLOCK, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force);
-        break;
-    case FORCE_UNIFORM:
-        k_adjoint<P, FORCE_UNIFORM><<<blocks, STEP_BLOCK, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force);
-        break;
-    default:
-        k_adjoint<P, FORCE_FIELD><<<blocks, STEP_BLOCK, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force);
+    const Shape sh = step_shape<St<P>::VEC>(g); // dense
+    if (sh.gx == 0) return cudaSuccess;
+    for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
+        const dim3 grid(sh.gx, sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u);
+        switch (ph.force_mode) {
+        case FORCE_NONE:
+            k_adjoint<P, FORCE_NONE><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
+            break;
+        case FORCE_UNIFORM:
+            k_adjoint<P, FORCE_UNIFORM><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
+            break;
+        default:
+            k_adjoint<P, FORCE_FIELD><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
+        }
     }
     return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ def _walls(moving_north=(0.0, 0.0)):
 # ---------------------------------------------------------------- lattice
 
 def test_lattice_matches_paper_golden(orc):
-    """c_i, w_i and the numbering as printed in Sec. 2.2 (Fig. D2Q9, Eq. f^eq)."""
+    """c_i, w_i and the numbering as printed in Sec. 2.2 (Fig. D2Q9, Eq. 6)."""
     cx, cy, w, opp = orc.lattice()
     rows = np.loadtxt(os.path.join(GOLDEN, "lattice_d2q9.txt"))
     assert np.array_equal(cx, rows[:, 1].astype(int))
@@ -47,7 +47,7 @@ def test_lattice_isotropy_closed_forms(orc):
 
 
 def test_equilibrium_moments_closed_form(orc):
-    """f^eq of Eq. (f^eq) has density rho and momentum rho u exactly."""
+    """f^eq of Eq. 6 has density rho and momentum rho u exactly."""
     s = orc.Setup(nx=8, ny=6, tau=0.7)
     mask, _ = orc.link_mask(s)
     rho = 1 + 0.1 * inputs.random_field((6, 8), 1)
@@ -139,7 +139,7 @@ def _ke(orc, s, mask, A):
 
 @pytest.mark.parametrize("n", [32, 64])
 def test_taylor_green_decay_rate(orc, n):
-    """Kinetic energy decays as exp(-4 nu k^2 t), nu = (tau - 1/2)/3 (Eq. omega)."""
+    """Kinetic energy decays as exp(-4 nu k^2 t), nu = (tau - 1/2)/3 (Eq. 5)."""
     tau, U = 0.8, 0.01
     s = orc.Setup(nx=n, ny=n, tau=tau)
     mask, _ = orc.link_mask(s)
