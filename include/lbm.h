@@ -195,6 +195,30 @@ lbm_status lbm_tile_map(const lbm_ctx *ctx, int32_t *h_tile_id, int32_t *h_nbr, 
 lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id, int32_t *h_nbr,
                         int *h_ntiles, long long *h_nfluid);
 
+/* Largest ny lbm_reduce_f_noalloc accepts (its scratch is sized for it). */
+#define LBM_NOALLOC_MAX_ROWS 16384
+
+/* lbm_reduce_f_noalloc -- the paper has no counterpart; this is a service
+ * for callers that must not allocate device memory at the moment they need a
+ * reduction: code running while its stream is captured into a CUDA graph,
+ * plugins whose host application owns every device buffer, real-time loops
+ * that never enter an allocator.  It computes, in FP64, over the nodes of a
+ * canonical array d_f [9][ny][nx] (compute type of `precision`: double for
+ * LBM_F64, float otherwise) whose d_mask [ny][nx] byte is not 0xFF (NULL:
+ * all nodes): d_out[0] = sum_i f_i, d_out[1..2] = sum_i c_i f_i (device
+ * pointer, 3 doubles), asynchronously on `stream`.  It needs no context and
+ * calls no allocator: its scratch is a static device array of
+ * LBM_NOALLOC_MAX_ROWS * 32 + 256 bytes (512.25 KiB) that every GPU loading
+ * the library keeps until the process exits.  ny > LBM_NOALLOC_MAX_ROWS (or
+ * a NULL pointer, nx or ny < 1) returns LBM_ERR_INVALID before any device
+ * work.  The first call on a device looks up the scratch array's device
+ * address (cudaGetSymbolAddress) and caches it per device: make that first
+ * call before any stream capture.  All calls share the scratch: calls that
+ * overlap on the GPU (other streams, other host threads) race.  Every call
+ * overwrites the scratch it reads, so nothing carries over between calls. */
+lbm_status lbm_reduce_f_noalloc(lbm_precision precision, const void *d_f, const uint8_t *d_mask, int nx, int ny,
+                                double *d_out, void *stream);
+
 long long lbm_fluid_nodes(const lbm_ctx *ctx);
 long long lbm_step_count(const lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status s);

@@ -92,6 +92,7 @@ def _load():
         "lbm_tile_map": ([_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int)], st),
         "lbm_geometry": ([_P, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_longlong)], st),
+        "lbm_reduce_f_noalloc": ([ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], st),
         "lbm_fluid_nodes": ([_vp], ctypes.c_longlong),
         "lbm_step_count": ([_vp], ctypes.c_longlong),
         "lbm_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -262,6 +263,24 @@ def lbm_geometry(p: lbm_params):
     if sparse:
         nbr = nbr[: nt.value].copy()
     return mask, tid, nbr, nf.value
+
+
+NOALLOC_MAX_ROWS = 16384  # LBM_NOALLOC_MAX_ROWS of lbm.h
+
+
+def lbm_reduce_f_noalloc(precision, f: torch.Tensor, mask: Optional[torch.Tensor], nx: int, ny: int,
+                         out: torch.Tensor, stream=None):
+    """Mass and momentum of canonical f [9, ny, nx] into out (3 doubles, on the
+    device) without any allocation in the library (see lbm.h); only pointers
+    are passed, nothing is allocated here either."""
+    if ny > NOALLOC_MAX_ROWS:
+        raise ValueError("lbm_reduce_f_noalloc: ny = %d exceeds LBM_NOALLOC_MAX_ROWS = %d (the size of its "
+                         "static scratch)" % (ny, NOALLOC_MAX_ROWS))
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    _check("lbm_reduce_f_noalloc", _load().lbm_reduce_f_noalloc(prec, _ptr(f), _ptr(mask), int(nx), int(ny),
+                                                                _ptr(out), stream or None))
 
 
 def lbm_fluid_nodes(ctx) -> int:
