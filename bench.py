@@ -165,6 +165,21 @@ def build_case(workload: str, n: int, precision: str):
     raise ValueError(workload)
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (every rank gets it)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_glups(nodes_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Node updates of all ranks (one replica each) per second, in 1e9."""
+    return nodes_per_rank * steps * world / seconds / 1e9
+
+
 def time_steps(sim, steps: int, warmup: int, stream):
     import torch
     sim.step(warmup)
@@ -211,12 +226,8 @@ def run_gpu_arm(args, rank, world, dist):
         end.record(stream)
         end.synchronize()
     barrier()
-    t = start.elapsed_time(end) / 1e3
+    t = max_over_ranks(start.elapsed_time(end) / 1e3, dist, dev)
     clocks = clk.summary()
-    if dist is not None:
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
     mass, _ = sim.reduce()
     if not np.isfinite(mass):
         raise RuntimeError("simulation diverged")
@@ -235,16 +246,12 @@ def run_gpu_arm(args, rank, world, dist):
     out_rho.copy_(r_out, non_blocking=True)
     out_u.copy_(u_out, non_blocking=True)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
     h2d = (0 if rho_h is None else rho_h.numel() * rho_h.element_size()) + \
           (0 if u_h is None else u_h.numel() * u_h.element_size())
     d2h = out_rho.numel() * out_rho.element_size() + out_u.numel() * out_u.element_size()
 
-    glups = nfluid * args.steps * world / t / 1e9
+    glups = whole_job_glups(nfluid, args.steps, world, t)
     step_s = t / args.steps
     algo = node_bytes(args.precision) * nfluid
     peak, peak_kind = peaks()
@@ -267,7 +274,7 @@ def run_gpu_arm(args, rank, world, dist):
                    "l2": "working set %.0f MB > 129 MB L2, no flush needed" %
                          (2 * 9 * BYTES_PER_VALUE[args.precision] * kw["nx"] * kw["ny"] / 1e6)},
         "roofline": roofline,
-        "e2e": {"value": round(nfluid * args.steps * world / t_e2e / 1e9, 3), "unit": "GLUPS",
+        "e2e": {"value": round(whole_job_glups(nfluid, args.steps, world, t_e2e), 3), "unit": "GLUPS",
                 "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
                 "what": "pinned host rho,u -> device, lbm_init_equilibrium, K x lbm_step, lbm_macros, "
                         "device -> pinned host rho,u"},
@@ -362,34 +369,159 @@ def cpu_baseline_leg(n: int):
 
 # ---------------------------------------------------------------- extra lines
 
+def _timed(sim, k, stream):
+    return time_steps(sim, k, 10, stream)
+
+
 def extra_measurements(args):
-    """Other rows of the metric at smaller step counts: precisions, AA, sparse."""
+    """Other rows of the metric, each with fewer steps: every precision and
+    pattern on the dense Taylor-Green box, the Poiseuille channel, the porous
+    sweep (phi 0.2 / 0.5 / 0.8, tiled layout, fluid-node GLUPS, with the
+    sparse computational efficiency eta_P of Eq. 9 against the same layout on
+    the all-fluid box), and the adjoint step cost on the cylinder channel."""
     import torch
-    from paper_2108_13241_gb300 import lbm
+    from paper_2108_13241_gb300 import inputs, lbm
     out = {}
     peak, _ = peaks()
     stream = torch.cuda.current_stream()
-    combos = [("tgv", 4096, "f64", "dense", "two_lattice", 100),
-              ("tgv", 4096, "f32", "dense", "aa", 500),
-              ("tgv", 4096, "f16s", "dense", "two_lattice", 500),
-              ("tgv", 4096, "f16s", "dense", "aa", 500),
-              ("poiseuille", 4096, "f32", "dense", "two_lattice", 500),
-              ("porous0.5", 4096, "f32", "sparse", "two_lattice", 300),
-              ("porous0.5", 4096, "f32", "dense", "two_lattice", 300)]
-    for wl, n, prec, layout, pattern, k in combos:
-        kw, rho, u, nf, wname = build_case(wl, n, prec)
+
+    def record(key, nf, k, t, prec):
+        g = nf * k / t / 1e9
+        out[key] = {"GLUPS": round(g, 3), "GBps_algorithmic": round(g * node_bytes(prec), 1),
+                    "frac_of_measured_hbm": round(g * node_bytes(prec) / peak, 4), "steps": k}
+        return g
+
+    def run(kw, rho, u, prec, layout, pattern, k):
         sim = lbm.LBM(precision=prec, layout=layout, pattern=pattern, **kw)
         sim.init_equilibrium(None if rho is None else torch.as_tensor(rho, dtype=sim.dtype, device="cuda"),
                              None if u is None else torch.as_tensor(u, dtype=sim.dtype, device="cuda"))
-        t = time_steps(sim, k, 10, stream)
-        g = nf * k / t / 1e9
-        out["%s/%s/%s/%s" % (wname, prec, layout, pattern)] = {
-            "GLUPS": round(g, 3), "GBps_algorithmic": round(g * node_bytes(prec), 1),
-            "frac_of_measured_hbm": round(g * node_bytes(prec) / peak, 4), "steps": k}
+        t = _timed(sim, k, stream)
         sim.close()
         del sim
         torch.cuda.empty_cache()
+        return t
+
+    n = 4096
+    rho, u = inputs.taylor_green(n, n, 0.05)
+    kw = dict(nx=n, ny=n, tau=0.8)
+    dense_geom = {}
+    for prec, layout, pattern, k in [("f64", "dense", "two_lattice", 100), ("f64", "dense", "aa", 100),
+                                     ("f32", "dense", "aa", 500), ("f16s", "dense", "two_lattice", 500),
+                                     ("f16s", "dense", "aa", 500), ("f32", "sparse", "two_lattice", 500),
+                                     ("f32", "sparse", "aa", 500), ("f16s", "sparse", "aa", 500)]:
+        t = run(kw, rho, u, prec, layout, pattern, k)
+        dense_geom[(prec, layout, pattern)] = record("taylor_green_%d/%s/%s/%s" % (n, prec, layout, pattern),
+                                                     n * n, k, t, prec)
+    fx, rho_p, u_p = inputs.poiseuille(n, n, 0.8, 0.05)
+    t = run(dict(nx=n, ny=n, tau=0.8, force=(fx, 0.0), periodic_y=False), rho_p, u_p, "f32", "dense",
+            "two_lattice", 500)
+    record("poiseuille_%d/f32/dense/two_lattice" % n, n * n, 500, t, "f32")
+    for phi in (0.2, 0.5, 0.8):
+        solid, achieved, _ = inputs.porous_discs(n, n, phi, rmin=8, rmax=32)
+        nf = int((solid == 0).sum())
+        kwp = dict(nx=n, ny=n, tau=0.8, solid=solid, force=(1e-6, 0.0), periodic_y=False)
+        combos = [("f32", "sparse", "two_lattice"), ("f32", "sparse", "aa"), ("f32", "dense", "two_lattice")]
+        if phi == 0.5:
+            combos += [("f16s", "sparse", "aa"), ("f64", "sparse", "two_lattice")]
+        for prec, layout, pattern in combos:
+            k = 100 if prec == "f64" else 300
+            t = run(kwp, None, None, prec, layout, pattern, k)
+            g = record("porous_phi%.2f_%d/%s/%s/%s" % (achieved, n, prec, layout, pattern), nf, k, t, prec)
+            if layout == "sparse" and (prec, layout, pattern) in dense_geom:
+                out["porous_phi%.2f_%d/%s/%s/%s" % (achieved, n, prec, layout, pattern)]["eta_P"] = round(
+                    g / dense_geom[(prec, layout, pattern)], 3)
+        out["porous_phi%.2f_%d/fluid_nodes" % (achieved, n)] = nf
+    out["adjoint_channel_512x256"] = adjoint_cost()
     return out
+
+
+def adjoint_cost():
+    """Cost of one adjoint step relative to one forward step on the
+    differentiable channel (512 x 256, 12 cylinders, FP32, T = 2000,
+    checkpoint every 45): backward wall time (recompute + adjoint) / T over
+    plain forward step time."""
+    import torch
+    from paper_2108_13241_gb300 import autograd as ag, inputs, lbm
+    nx, ny, T, K = 512, 256, 2000, 45
+    solid, _ = inputs.channel_cylinders(nx, ny, count=12, rmin=6, rmax=12, clearance=2)
+    F = np.zeros((2, ny, nx), np.float32)
+    F[0] = 1e-5
+    ut = torch.as_tensor(inputs.target_velocity(nx, ny, solid), dtype=torch.float32, device="cuda")
+    sim = lbm.LBM(nx, ny, 0.8, solid=solid, periodic_y=False, precision="f32")
+    Ft = torch.as_tensor(F, device="cuda")
+    sim.set_force(Ft)
+    stream = torch.cuda.current_stream()
+    t_step = time_steps(sim, T, 20, stream) / T
+    fl = torch.as_tensor(solid == 0, device="cuda")
+    for _ in range(2):  # the first pass warms the allocator (checkpoint buffers)
+        sim.init_equilibrium(None, None)
+        Fg = Ft.clone().requires_grad_(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        rho, u = ag.simulate(sim, T, None, Fg, K=K)
+        loss = (((u - ut) ** 2).sum(0) * fl).sum() / fl.sum()
+        ev[1].record(stream)
+        loss.backward()
+        ev[2].record(stream)
+        ev[2].synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1]) / 1e3
+    t_bwd = ev[1].elapsed_time(ev[2]) / 1e3
+    return {"forward_step_us": round(t_step * 1e6, 2),
+            "checkpointed_forward_step_us": round(t_fwd / T * 1e6, 2),
+            "backward_step_us": round(t_bwd / T * 1e6, 2),
+            "adjoint_over_forward": round(t_bwd / T / t_step, 3),
+            "grad_finite": bool(torch.isfinite(Fg.grad).all().item())}
+
+
+def precision_sweep(n: int = 8192, steps: int = 5000):
+    """Precision sweep: dense Taylor-Green (U 0.05) and the porous medium
+    (phi 0.3, same disc generator, F = 1e-6) at n^2, FP64 vs FP32 vs FP16s
+    storage, `steps` steps each; the error is the relative L2 norm of u over
+    fluid nodes against the FP64 GPU run (itself pinned to the CPU oracle on
+    the smaller configurations), reported beside GLUPS."""
+    import torch
+    from paper_2108_13241_gb300 import inputs, lbm
+    stream = torch.cuda.current_stream()
+    res = {}
+    rho, u = inputs.taylor_green(n, n, 0.05)
+    solid, achieved, _ = inputs.porous_discs(n, n, 0.3, rmin=8, rmax=32)
+    cases = [("taylor_green_%d" % n, dict(nx=n, ny=n, tau=0.8), rho, u, n * n, None),
+             ("porous_phi%.2f_%d" % (achieved, n),
+              dict(nx=n, ny=n, tau=0.8, solid=solid, force=(1e-6, 0.0), periodic_y=False),
+              None, None, int((solid == 0).sum()), torch.as_tensor(solid == 0, device="cuda"))]
+    for name, kw, r0, u0, nf, fl in cases:
+        ref_u = None
+        for prec, layout, pattern in (("f64", "dense", "aa"), ("f32", "dense", "aa"),
+                                      ("f16s", "dense", "aa")):
+            if name.startswith("porous"):
+                layout = "sparse"
+            sim = lbm.LBM(precision=prec, layout=layout, pattern=pattern, **kw)
+            sim.init_equilibrium(None if r0 is None else torch.as_tensor(r0, dtype=sim.dtype, device="cuda"),
+                                 None if u0 is None else torch.as_tensor(u0, dtype=sim.dtype, device="cuda"))
+            torch.cuda.synchronize()
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            sim.step(steps)
+            end.record(stream)
+            end.synchronize()
+            t = start.elapsed_time(end) / 1e3
+            _, uu = sim.macros()
+            uu = uu.double()
+            if fl is not None:
+                uu = uu * fl
+            entry = {"GLUPS": round(nf * steps / t / 1e9, 3), "layout": layout, "pattern": pattern}
+            if ref_u is None:
+                ref_u = uu
+            else:
+                entry["rel_l2_u_vs_f64"] = float(torch.linalg.vector_norm(uu - ref_u) /
+                                                 torch.linalg.vector_norm(ref_u))
+            res["%s/%s" % (name, prec)] = entry
+            sim.close()
+            del sim, uu
+            torch.cuda.empty_cache()
+    return {"sweep": "precision", "steps": steps, "results": res}
 
 
 def main():
@@ -405,8 +537,15 @@ def main():
     ap.add_argument("--pattern", default="two_lattice", choices=["two_lattice", "aa"])
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the 8192^2 FP64/FP32/FP16s precision sweep instead of the benchmark")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.sweep:
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(precision_sweep()), flush=True)
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -79,7 +79,9 @@ typedef struct {
 
 typedef struct {
     int nx, ny;               /* nx % 16 == 0; LBM_SPARSE_TILE16 with a
-                                 periodic y axis also needs ny % 16 == 0   */
+                                 periodic y axis also needs ny % 16 == 0;
+                                 9 * (stored nodes) < 2^32 (32-bit element
+                                 indices: up to ~21800^2 nodes)             */
     const uint8_t *solid;     /* HOST [ny][nx], nonzero = solid; NULL = all
                                  fluid; read during lbm_workspace_bytes and
                                  lbm_create only                           */

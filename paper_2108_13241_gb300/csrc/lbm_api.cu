@@ -51,7 +51,9 @@ const char *check_params(const lbm_params *p) {
     if (!p) return "params is NULL";
     if (p->nx < 16 || p->nx % 16) return "nx must be a positive multiple of 16";
     if (p->ny < 1) return "ny must be >= 1";
-    if ((long long)p->nx * p->ny > (1ll << 30)) return "nx*ny must be <= 2^30";
+    // element indices of the lattices and of canonical [9][ny][nx] arrays are
+    // 32-bit in the kernels
+    if (9ll * p->nx * p->ny >= (1ll << 32)) return "9*nx*ny must be < 2^32";
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be > 0.5";
     if (!std::isfinite(p->fx) || !std::isfinite(p->fy)) return "force must be finite";
     if ((p->west.periodic != 0) != (p->east.periodic != 0))
@@ -183,6 +185,7 @@ lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes) {
     std::vector<int32_t> tid, nbr, txy;
     Plan pl;
     make_plan(*p, mask, tid, nbr, txy, pl);
+    if (9ll * pl.nslot >= (1ll << 32)) return LBM_ERR_INVALID;
     *bytes = pl.total;
     return LBM_OK;
 }
@@ -200,6 +203,10 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     std::vector<int32_t> txy;
     Plan pl;
     make_plan(*p, c->mask, c->tile_id, c->nbr, txy, pl);
+    if (9ll * pl.nslot >= (1ll << 32)) {
+        delete c;
+        return LBM_ERR_INVALID;
+    }
     if (bytes < pl.total) {
         delete c;
         return LBM_ERR_OOM;

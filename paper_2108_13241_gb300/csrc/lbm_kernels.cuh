@@ -76,6 +76,17 @@ template <int BYTES> struct VecWord;
 template <> struct VecWord<16> { typedef uint4 T; static __device__ __forceinline__ uint4 zero() { return make_uint4(0, 0, 0, 0); } };
 template <> struct VecWord<8> { typedef uint2 T; static __device__ __forceinline__ uint2 zero() { return make_uint2(0, 0); } };
 
+// The same storage with a different number of nodes per thread.
+template <int P, int V> struct StV : St<P> {
+    enum { VEC = V };
+};
+// Nodes per thread of the step kernel: FP32 with a link mask moves 2 nodes
+// (8-byte vectors) so the bounce-back state fits 4 blocks per SM; otherwise
+// one 16-byte (FP64, FP32) or 8-byte (FP16s) vector.
+template <int P, bool HAS_MASK> struct StepVec {
+    enum { value = (P == LBM_F32 && HAS_MASK) ? 2 : St<P>::VEC };
+};
+
 template <class R, int VEC> union V16 {
     typename VecWord<(int)sizeof(R) * VEC>::T u;
     R v[VEC];
@@ -141,43 +152,46 @@ __device__ __forceinline__ int pick3(int o, int a, int b, int c) { return o < 0 
 
 // Dense SoA f[slot][ny][nx]; thread = VEC nodes (x0..x0+VEC-1, y).
 template <int VEC> struct DenseAddr {
+    enum { VEC_ = VEC };
     int x0, y, xv, nvx, nx, ny;
-    bool px, py, valid;
-    long long nslot;
+    bool valid;
+    unsigned nslot; // element indices fit 32 bits (checked at create)
     const uint8_t *mask;
+    int roff[3];    // (row y-1, y, y+1) * nx: wrapped (periodic) or clamped (wall)
+    int lcol, rcol; // columns x0 - 1 and x0 + VEC, wrapped or clamped
 
-    // 2-D launch: (vector column, row) = (blockIdx.x * blockDim.x + tid, row)
+    // 2-D launch: (vector column, row) = (blockIdx.x * blockDim.x + tid, row).
+    // Everything that depends on the wrap is resolved here, branch-free.
     __device__ __forceinline__ DenseAddr(const Geo &g, int col, int row_) {
         nx = g.nx;
         ny = g.ny;
-        px = g.periodic_x;
-        py = g.periodic_y;
-        nslot = g.nslot;
+        nslot = (unsigned)g.nslot;
         mask = g.mask;
         nvx = nx / VEC;
         valid = col < nvx;
         xv = valid ? col : nvx - 1;
         y = row_;
         x0 = xv * VEC;
+        const bool px = g.periodic_x, py = g.periodic_y;
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+            int r = y + d;
+            r = r < 0 ? (py ? r + ny : 0) : r;
+            r = r >= ny ? (py ? r - ny : ny - 1) : r;
+            roff[d + 1] = r * nx;
+        }
+        const int l = x0 - 1, rr = x0 + VEC;
+        lcol = l < 0 ? (px ? nx - 1 : 0) : l;
+        rcol = rr >= nx ? (px ? 0 : nx - 1) : rr;
     }
-    __device__ __forceinline__ int row(int dy) const {
-        int r = y + dy;
-        if (r < 0) r = py ? r + ny : 0;
-        else if (r >= ny) r = py ? r - ny : ny - 1;
-        return r;
+    // aligned vector of slot at (x0, y + dy), dy in {-1, 0, 1}
+    __device__ __forceinline__ unsigned vidx(int slot, int dy) const {
+        return (unsigned)slot * nslot + (unsigned)(roff[dy + 1] + x0);
     }
-    __device__ __forceinline__ int col(int c) const {
-        if (c < 0) c = px ? c + nx : 0;
-        else if (c >= nx) c = px ? c - nx : nx - 1;
-        return c;
-    }
-    // aligned vector of slot at (x0, y + dy)
-    __device__ __forceinline__ long long vidx(int slot, int dy) const {
-        return slot * nslot + (long long)row(dy) * nx + x0;
-    }
-    // element (x0 + k + dx, y + dy), wrapped (periodic) or clamped (wall)
-    __device__ __forceinline__ long long eidx(int slot, int k, int dx, int dy) const {
-        return slot * nslot + (long long)row(dy) * nx + col(x0 + k + dx);
+    // element (x0 + k + dx, y + dy), k + dx in [-1, VEC], dy in {-1, 0, 1}
+    __device__ __forceinline__ unsigned eidx(int slot, int k, int dx, int dy) const {
+        const int c = (k + dx < 0) ? lcol : ((k + dx >= VEC) ? rcol : x0 + k + dx);
+        return (unsigned)slot * nslot + (unsigned)(roff[dy + 1] + c);
     }
     __device__ __forceinline__ bool left_in_warp(int lane) const { return lane > 0 && xv > 0; }
     __device__ __forceinline__ bool right_in_warp(int lane) const { return lane < 31 && xv < nvx - 1; }
@@ -191,11 +205,15 @@ template <int VEC> struct DenseAddr {
 // Tiled sparse f[tile][slot][16][16]; thread = VEC nodes of one tile row.
 // nbr3 is the device table [tile][3*(oy+1) + (ox+1)] (absent -> -1).
 template <int VEC> struct TileAddr {
-    enum { TPR = TILE / VEC, TPT = TILE * (TILE / VEC) };
+    enum { VEC_ = VEC, TPR = TILE / VEC, TPT = TILE * (TILE / VEC) };
     int t, lx0, ly, xv, tx, ty, nx, ny;
     bool valid;
-    int nb[9];
     const uint8_t *mask;
+    // element index (slot 0) of this thread's first node in rows ly-1, ly,
+    // ly+1 (rowb), and of the nodes just left (lb) and right (rb) of the
+    // thread's vector in those rows, in whatever tile holds them (32-bit:
+    // 9 * 256 * tiles < 2^32 is checked at create)
+    unsigned rowb[3], lb[3], rb[3];
 
     // 1-D launch over tiles (TPT threads per tile); the row argument is unused
     __device__ __forceinline__ TileAddr(const Geo &g, int gtid, int) {
@@ -213,25 +231,34 @@ template <int VEC> struct TileAddr {
         const int txy = __ldg(g.tile_xy + t);
         tx = txy & 0xFFFF;
         ty = txy >> 16;
+        int nb[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             const int n = __ldg(g.nbr + 9 * (long long)t + j);
             nb[j] = n < 0 ? t : n; // absent: any valid tile, the value is unused
         }
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+            const int r = ly + d;
+            const int oy = r < 0 ? -1 : (r >= TILE ? 1 : 0);
+            const int rr = (r & (TILE - 1)) * TILE;
+            const int tc = pick3(oy, nb[1], nb[4], nb[7]);
+            const int tl_ = pick3(oy, nb[0], nb[3], nb[6]);
+            const int tr_ = pick3(oy, nb[2], nb[5], nb[8]);
+            const unsigned base = (unsigned)tc * (9u * TILE_N) + (unsigned)rr;
+            rowb[d + 1] = base + lx0;
+            lb[d + 1] = xv == 0 ? (unsigned)tl_ * (9u * TILE_N) + (unsigned)(rr + TILE - 1) : base + lx0 - 1;
+            rb[d + 1] = xv == TPR - 1 ? (unsigned)tr_ * (9u * TILE_N) + (unsigned)rr : base + lx0 + VEC;
+        }
     }
-    __device__ __forceinline__ int tile_at(int ox, int oy) const {
-        return pick3(oy, pick3(ox, nb[0], nb[1], nb[2]), pick3(ox, nb[3], nb[4], nb[5]),
-                     pick3(ox, nb[6], nb[7], nb[8]));
+    __device__ __forceinline__ unsigned vidx(int slot, int dy) const {
+        return rowb[dy + 1] + (unsigned)(slot * TILE_N);
     }
-    __device__ __forceinline__ long long at(int slot, int c, int r) const {
-        const int ox = c < 0 ? -1 : (c >= TILE ? 1 : 0);
-        const int oy = r < 0 ? -1 : (r >= TILE ? 1 : 0);
-        const int tt = tile_at(ox, oy);
-        return ((long long)tt * 9 + slot) * TILE_N + (r & (TILE - 1)) * TILE + (c & (TILE - 1));
-    }
-    __device__ __forceinline__ long long vidx(int slot, int dy) const { return at(slot, lx0, ly + dy); }
-    __device__ __forceinline__ long long eidx(int slot, int k, int dx, int dy) const {
-        return at(slot, lx0 + k + dx, ly + dy);
+    // element (x0 + k + dx, y + dy), k + dx in [-1, VEC], dy in {-1, 0, 1}
+    __device__ __forceinline__ unsigned eidx(int slot, int k, int dx, int dy) const {
+        if (k + dx < 0) return lb[dy + 1] + (unsigned)(slot * TILE_N);
+        if (k + dx >= VEC) return rb[dy + 1] + (unsigned)(slot * TILE_N);
+        return rowb[dy + 1] + (unsigned)(slot * TILE_N + k + dx);
     }
     __device__ __forceinline__ bool left_in_warp(int) const { return xv > 0; }
     __device__ __forceinline__ bool right_in_warp(int) const { return xv < TPR - 1; }
@@ -465,20 +492,59 @@ __device__ __forceinline__ void node_values(const V16<typename S::R, S::VEC> raw
     f[8] = S::dec(pulled<S, 8, K>(raw, edge, MODE));
 }
 
+// Stored value of slot s at the thread's own node k.  Slots 0, 1, 3 are in
+// the gathered vectors already (their pulls come from the node's own row,
+// unshifted in memory); the others were preloaded into `own` when some node
+// of the vector bounces a link that needs them.
+template <class S, int MODE>
+__device__ __forceinline__ typename S::R own_value(const V16<typename S::R, S::VEC> raw[9],
+                                                   const V16<typename S::R, S::VEC> own[9], int s, int k) {
+    if (s == 0 || s == 1 || s == 3) return MODE == MODE_TWO_LATTICE ? raw[s].v[k] : raw[opp(s)].v[k];
+    return own[s].v[k];
+}
+
+// Own-node slot that half-way bounce-back of link i reads: the post-collision
+// value of link opp(i) at x, held in slot opp(i) (two-lattice) or in slot i
+// (AA gather/scatter step, where slot i of x holds link opp(i)'s value).
+template <int MODE> __host__ __device__ constexpr int bounce_slot(int i) {
+    return MODE == MODE_TWO_LATTICE ? opp(i) : i;
+}
+
+// Loads, right after the gather, the own-node vectors of the slots that the
+// vector's bounced links need (union of the fluid nodes' mask bits).
+template <class S, int MODE, class A>
+__device__ __forceinline__ void preload_own(const A &ad, const typename S::R *src, unsigned long long mv,
+                                            V16<typename S::R, S::VEC> own[9]) {
+    constexpr int VEC = S::VEC;
+    constexpr bool NC = (MODE == MODE_TWO_LATTICE);
+    unsigned bits = 0;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        const unsigned m = (unsigned)((mv >> (8 * k)) & 0xFFu);
+        bits |= (m == 0xFFu) ? 0u : m;
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int sl = bounce_slot<MODE>(i);
+        if (sl == 0 || sl == 1 || sl == 3) continue;
+        if (bits & (1u << (i - 1))) own[sl] = ld16<NC, typename S::R, VEC>(src + ad.vidx(sl, 0));
+    }
+}
+
 // Half-way bounce-back for the links of node k whose mask bit is set:
 // f'_i = (stored post-collision value of link opp(i) at x) + wall term.
 template <class S, int MODE, class A>
-__device__ __forceinline__ void bounce(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
-                                       int k, unsigned m, typename S::C f[9]) {
+__device__ __forceinline__ void bounce(const Geo &g, const Phys &ph, const A &ad,
+                                       const V16<typename S::R, S::VEC> raw[9],
+                                       const V16<typename S::R, S::VEC> own[9], int k, unsigned m,
+                                       typename S::C f[9]) {
     typedef typename S::C C;
-    constexpr bool NC = (MODE == MODE_TWO_LATTICE);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         if (m & (1u << (i - 1))) {
             C v;
-            if (MODE == MODE_TWO_LATTICE) v = S::dec(ld1<NC>(src + ad.eidx(opp(i), k, 0, 0)));
-            else if (MODE == MODE_AA_PULLPUSH) v = S::dec(ld1<NC>(src + ad.eidx(i, k, 0, 0)));
-            else v = f[i];
+            if (MODE == MODE_AA_LOCAL) v = f[i];
+            else v = S::dec(own_value<S, MODE>(raw, own, bounce_slot<MODE>(i), k));
             if (ph.has_wall) v = v + PC<C>::wt(ph, wall_side(g, ad.gx(k), ad.gy(), i), i);
             f[i] = v;
         }
@@ -496,29 +562,27 @@ __device__ __forceinline__ void load_force(const Geo &g, const Phys &ph, const A
         Fy[k] = PC<C>::fy(ph);
     }
     if (FORCE == FORCE_FIELD && active && ad.in_domain()) {
+        // VEC values of each component: one 8- or 16-byte vector
+        static_assert(VEC * sizeof(C) == 8 || VEC * sizeof(C) == 16, "force vector width");
         const C *F = reinterpret_cast<const C *>(ph.force);
         const long long n = ad.node(0);
-        constexpr int CH = VEC * (int)sizeof(C) / 16; // 16-byte chunks
+        const V16<C, VEC> a = ld16<true, C, VEC>(F + n);
+        const V16<C, VEC> b = ld16<true, C, VEC>(F + g.nnode + n);
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            V16<C, 16 / sizeof(C)> a = ld16<true, C, 16 / sizeof(C)>(F + n + c * (16 / sizeof(C)));
-            V16<C, 16 / sizeof(C)> b = ld16<true, C, 16 / sizeof(C)>(F + g.nnode + n + c * (16 / sizeof(C)));
-#pragma unroll
-            for (int j = 0; j < (int)(16 / sizeof(C)); ++j) {
-                Fx[c * (16 / sizeof(C)) + j] = a.v[j];
-                Fy[c * (16 / sizeof(C)) + j] = b.v[j];
-            }
+        for (int k = 0; k < VEC; ++k) {
+            Fx[k] = a.v[k];
+            Fy[k] = b.v[k];
         }
     }
 }
 
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE, int K>
-__device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad, const typename St<P>::R *src,
-                                        unsigned long long mv, const V16<typename St<P>::R, St<P>::VEC> raw[9],
-                                        const typename St<P>::R edge[9], const typename St<P>::C Fx[],
-                                        const typename St<P>::C Fy[], const Coef<typename St<P>::C> &co,
-                                        V16<typename St<P>::R, St<P>::VEC> out[9]) {
-    typedef St<P> S;
+template <class S, class A, int MODE, bool HAS_MASK, int FORCE, int K>
+__device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad,
+                                        const V16<typename S::R, S::VEC> own[9],
+                                        unsigned long long mv, const V16<typename S::R, S::VEC> raw[9],
+                                        const typename S::R edge[9], const typename S::C Fx[],
+                                        const typename S::C Fy[], const Coef<typename S::C> &co,
+                                        V16<typename S::R, S::VEC> out[9]) {
     typedef typename S::C C;
     C f[9];
     node_values<S, K, MODE>(raw, edge, f);
@@ -528,34 +592,35 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
         for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(C(0));
         return;
     }
-    if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, src, K, m, f);
+    if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, raw, own, K, m, f);
     collide<C, FORCE != FORCE_NONE>(f, Fx[K], Fy[K], co);
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);
 }
 
 // Nodes K0 .. K1-1 of the thread, in order (compile-time unrolled).
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE, int K, int K1>
+template <class S, class A, int MODE, bool HAS_MASK, int FORCE, int K, int K1>
 struct NodeRange {
     static __device__ __forceinline__ void run(const Geo &g, const Phys &ph, const A &ad,
-                                               const typename St<P>::R *src, unsigned long long mv,
-                                               const V16<typename St<P>::R, St<P>::VEC> raw[9],
-                                               const typename St<P>::R edge[9], const typename St<P>::C Fx[],
-                                               const typename St<P>::C Fy[], const Coef<typename St<P>::C> &co,
-                                               V16<typename St<P>::R, St<P>::VEC> out[9]) {
+                                               const V16<typename S::R, S::VEC> own[9],
+                                               unsigned long long mv,
+                                               const V16<typename S::R, S::VEC> raw[9],
+                                               const typename S::R edge[9], const typename S::C Fx[],
+                                               const typename S::C Fy[], const Coef<typename S::C> &co,
+                                               V16<typename S::R, S::VEC> out[9]) {
         if constexpr (K < K1) {
-            do_node<P, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
-            NodeRange<P, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
+            do_node<S, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, out);
+            NodeRange<S, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, out);
         }
     }
 };
 
 // Stores of the thread's VEC nodes for the three step kinds.
-template <int P, class A, int MODE, bool HAS_MASK>
-__device__ __forceinline__ void store_all(const A &ad, typename St<P>::R *dst, unsigned long long mv,
-                                           const V16<typename St<P>::R, St<P>::VEC> out[9]) {
-    typedef typename St<P>::R R;
-    constexpr int VEC = St<P>::VEC;
+template <class S, class A, int MODE, bool HAS_MASK>
+__device__ __forceinline__ void store_all(const A &ad, typename S::R *dst, unsigned long long mv,
+                                           const V16<typename S::R, S::VEC> out[9]) {
+    typedef typename S::R R;
+    constexpr int VEC = S::VEC;
     if constexpr (MODE == MODE_TWO_LATTICE) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) st16<R, VEC>(dst + ad.vidx(i, 0), out[i]);
@@ -588,10 +653,19 @@ __device__ __forceinline__ void store_all(const A &ad, typename St<P>::R *dst, u
     }
 }
 
+// Blocks of 256 threads each SM must hold (the register cap that follows):
+// the FP32 / FP16s step is memory-latency bound, so occupancy is fixed here
+// rather than left to the register allocator -- 4 blocks (<= 64 registers)
+// without a mask and for FP32 with a mask (2 nodes per thread), 3 blocks
+// (<= 80) for FP16s with a mask.  FP64 is ALU-bound and left free.
+template <int P, bool HAS_MASK> struct MinBlocks {
+    enum { value = P == LBM_F64 ? 1 : ((HAS_MASK && P == LBM_F16S) ? 3 : 4) };
+};
+
 template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
-__global__ void __launch_bounds__(STEP_BLOCK) k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v,
-                                                     int y0) {
-    typedef St<P> S;
+__global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
+    k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0) {
+    typedef StV<P, A::VEC_> S;
     typedef typename S::R R;
     typedef typename S::C C;
     constexpr int VEC = S::VEC;
@@ -609,14 +683,16 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_step(const Geo g, const Phys ph,
     R edge[9];
     gather_raw<S, MODE>(ad, src, active, lane, raw, edge);
     if (!active) return; // no collective operation follows
+    V16<R, VEC> own[9];
+    if (HAS_MASK && MODE != MODE_AA_LOCAL && mv != 0ull) preload_own<S, MODE>(ad, src, mv, own);
 
     C Fx[VEC], Fy[VEC];
     load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
     const Coef<C> co(ph);
 
     V16<R, VEC> out[9];
-    NodeRange<P, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, src, mv, raw, edge, Fx, Fy, co, out);
-    store_all<P, A, MODE, HAS_MASK>(ad, dst, mv, out);
+    NodeRange<S, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, out);
+    store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
 }
 
 // ------------------------------------------------------------- adjoint kernel
@@ -630,12 +706,12 @@ template <int P, int FORCE>
 __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys ph, const void *state_v,
                                                         const void *lam_in_v, void *lam_out_v, void *gF_v,
                                                         int y0) {
-    typedef St<P> S;
+    typedef StV<P, StepVec<P, true>::value> S; // FP32: 2 nodes per thread
     typedef typename S::R R;
     typedef typename S::C C;
     constexpr int VEC = S::VEC;
-    constexpr int LC = 16 / (int)sizeof(C); // compute values per 16 bytes
-    constexpr int CH = VEC / LC;            // 16-byte chunks per thread per slot
+    constexpr int LC = VEC < 16 / (int)sizeof(C) ? VEC : 16 / (int)sizeof(C); // values per vector
+    constexpr int CH = VEC / LC;                                               // vectors per slot
     const R *src = reinterpret_cast<const R *>(state_v);
     const C *lin = reinterpret_cast<const C *>(lam_in_v);
     C *lout = reinterpret_cast<C *>(lam_out_v);
@@ -650,6 +726,8 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
     V16<R, VEC> raw[9];
     R edge[9];
     gather_raw<S, MODE_TWO_LATTICE>(ad, src, active, lane, raw, edge);
+    V16<R, VEC> own[9];
+    if (mv != 0ull) preload_own<S, MODE_TWO_LATTICE>(ad, src, mv, own);
     C Fx[VEC], Fy[VEC];
     load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
     const C omega = PC<C>::omega(ph);
@@ -671,7 +749,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
         for (int c = 0; c < CH; ++c) {
             V16<C, LC> v;
             if (active) v = ld16<true, C, LC>(lin + j * g.nnode + n0 + c * LC);
-            else v.u = make_uint4(0, 0, 0, 0);
+            else zero16(v);
 #pragma unroll
             for (int q = 0; q < LC; ++q) lam[j][c * LC + q] = v.v[q];
         }
@@ -682,7 +760,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
         if (m != 0xFFu) {                                                                 \
             C f[9];                                                                       \
             node_values<S, ((K) < VEC ? (K) : 0), MODE_TWO_LATTICE>(raw, edge, f);        \
-            if (m != 0u) bounce<S, MODE_TWO_LATTICE>(g, ph, ad, src, (K), m, f);          \
+            if (m != 0u) bounce<S, MODE_TWO_LATTICE>(g, ph, ad, raw, own, (K), m, f);     \
             C l[9], gg[9];                                                                \
             for (int j = 0; j < 9; ++j) l[j] = lam[j][(K)];                               \
             adjoint_node<C, FORCE != FORCE_NONE>(f, l, Fx[(K)], Fy[(K)], omega, gg,       \
@@ -707,7 +785,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
         const unsigned long long rep = j == 0 ? 0ull : mask_rep<VEC>(j - 1);
         if (cx(j) == 0 && (j == 0 || (mv & rep) == 0ull)) {
             // all VEC targets are the aligned vector at (x0, y - c_y)
-            const long long base = j * g.nnode + (long long)ad.row(-cy(j)) * g.nx + ad.x0;
+            const long long base = j * g.nnode + ad.roff[1 - cy(j)] + ad.x0;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 V16<C, LC> v;
@@ -1040,7 +1118,7 @@ template <int VEC> static Shape step_shape(const Geo &g) {
 
 template <int P, class A, int MODE, bool HM, int F>
 static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, cudaStream_t s) {
-    const Shape sh = step_shape<St<P>::VEC>(g);
+    const Shape sh = step_shape<A::VEC_>(g);
     if (sh.gx == 0) return cudaSuccess;
     for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
         const unsigned gy = sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u;
@@ -1067,12 +1145,12 @@ static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void 
 
 template <int P>
 cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, cudaStream_t s) {
-    constexpr int VEC = St<P>::VEC;
+    constexpr int VM = StepVec<P, true>::value, VN = StepVec<P, false>::value;
     if (g.layout == LBM_DENSE) {
-        if (g.has_mask) return step_mode<P, DenseAddr<VEC>, true>(g, ph, mode, src, dst, s);
-        return step_mode<P, DenseAddr<VEC>, false>(g, ph, mode, src, dst, s);
+        if (g.has_mask) return step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, s);
+        return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, s);
     }
-    return step_mode<P, TileAddr<VEC>, true>(g, ph, mode, src, dst, s);
+    return step_mode<P, TileAddr<VM>, true>(g, ph, mode, src, dst, s);
 }
 
 static inline unsigned node_blocks(const Geo &g) {
@@ -1110,7 +1188,7 @@ cudaError_t launch_reduce(const Geo &g, const Phys &ph, int phase, int kind, con
 template <int P>
 cudaError_t launch_adjoint(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
                            void *grad_force, cudaStream_t s) {
-    const Shape sh = step_shape<St<P>::VEC>(g); // dense
+    const Shape sh = step_shape<StepVec<P, true>::value>(g); // dense, as k_adjoint
     if (sh.gx == 0) return cudaSuccess;
     for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
         const dim3 grid(sh.gx, sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u);

@@ -86,7 +86,7 @@ def _stamp_disc(solid: np.ndarray, cx: float, cy: float, r: float, periodic_x: b
 
 def porous_discs(nx: int, ny: int, porosity: float, rmin: float = 8.0, rmax: float = 32.0,
                  seed: int = GEOMETRY_SEED, periodic_x: bool = True,
-                 max_rejections: int = 10_000):
+                 max_rejections: int = 1_000):
     """Random-disc porous medium with porosity phi = fluid nodes / all nodes.
 
     Radii are uniform reals in [rmin, rmax]; centres uniform reals over the

@@ -53,7 +53,10 @@ def test_one_step_from_gpu_state_matches_oracle_full_size(L, orc, tgv, precision
     assert err <= tol, err
     sim.step(100)
     m1, _ = sim.reduce()
-    assert abs(m1 - m0) <= 1e-9 * m0
+    # FP32 storage keeps mass to ~1e-9 relative over 100 steps; binary16
+    # storage rounds each of the 9 stored values independently (half an ulp
+    # of f_i - w_i, ~4e-6), so mass performs a small random walk
+    assert abs(m1 - m0) <= (1e-9 if precision == "f32" else 1e-5) * m0
 
 
 def test_full_size_aa_equals_two_lattice_fp32(L, tgv):
