@@ -474,29 +474,16 @@ def adjoint_cost():
             "grad_finite": bool(torch.isfinite(Fg.grad).all().item())}
 
 
-def precision_sweep(n: int = 8192, steps: int = 5000):
-    """Precision sweep: dense Taylor-Green (U 0.05) and the porous medium
-    (phi 0.3, same disc generator, F = 1e-6) at n^2, FP64 vs FP32 vs FP16s
-    storage, `steps` steps each; the error is the relative L2 norm of u over
-    fluid nodes against the FP64 GPU run (itself pinned to the CPU oracle on
-    the smaller configurations), reported beside GLUPS."""
+def _accuracy_runs(cases, steps, precisions, stream):
+    """For each case: GLUPS of each precision and the relative L2 norm of u
+    over fluid nodes against the FP64 GPU run of the same case."""
     import torch
-    from paper_2108_13241_gb300 import inputs, lbm
-    stream = torch.cuda.current_stream()
+    from paper_2108_13241_gb300 import lbm
     res = {}
-    rho, u = inputs.taylor_green(n, n, 0.05)
-    solid, achieved, _ = inputs.porous_discs(n, n, 0.3, rmin=8, rmax=32)
-    cases = [("taylor_green_%d" % n, dict(nx=n, ny=n, tau=0.8), rho, u, n * n, None),
-             ("porous_phi%.2f_%d" % (achieved, n),
-              dict(nx=n, ny=n, tau=0.8, solid=solid, force=(1e-6, 0.0), periodic_y=False),
-              None, None, int((solid == 0).sum()), torch.as_tensor(solid == 0, device="cuda"))]
-    for name, kw, r0, u0, nf, fl in cases:
+    for name, kw, r0, u0, nf, fl, layout in cases:
         ref_u = None
-        for prec, layout, pattern in (("f64", "dense", "aa"), ("f32", "dense", "aa"),
-                                      ("f16s", "dense", "aa")):
-            if name.startswith("porous"):
-                layout = "sparse"
-            sim = lbm.LBM(precision=prec, layout=layout, pattern=pattern, **kw)
+        for prec in ("f64",) + tuple(precisions):
+            sim = lbm.LBM(precision=prec, layout=layout, pattern="aa", **kw)
             sim.init_equilibrium(None if r0 is None else torch.as_tensor(r0, dtype=sim.dtype, device="cuda"),
                                  None if u0 is None else torch.as_tensor(u0, dtype=sim.dtype, device="cuda"))
             torch.cuda.synchronize()
@@ -511,7 +498,7 @@ def precision_sweep(n: int = 8192, steps: int = 5000):
             uu = uu.double()
             if fl is not None:
                 uu = uu * fl
-            entry = {"GLUPS": round(nf * steps / t / 1e9, 3), "layout": layout, "pattern": pattern}
+            entry = {"GLUPS": round(nf * steps / t / 1e9, 3), "layout": layout, "pattern": "aa"}
             if ref_u is None:
                 ref_u = uu
             else:
@@ -521,7 +508,36 @@ def precision_sweep(n: int = 8192, steps: int = 5000):
             sim.close()
             del sim, uu
             torch.cuda.empty_cache()
-    return {"sweep": "precision", "steps": steps, "results": res}
+    return res
+
+
+def precision_sweep(n: int = 8192, steps: int = 5000):
+    """Precision sweep: dense Taylor-Green (U 0.05) and the porous medium
+    (phi 0.3, same disc generator, F = 1e-6) at n^2, FP64 vs FP32 vs FP16s
+    storage, `steps` steps each; plus the dense Taylor-Green and Poiseuille
+    boxes at 1024^2 .. 4096^2 after 1000 steps.  Errors are relative L2 norms
+    of u over fluid nodes against the FP64 GPU run (itself pinned to the CPU
+    oracle on the smaller configurations), reported beside GLUPS."""
+    import torch
+    from paper_2108_13241_gb300 import inputs
+    stream = torch.cuda.current_stream()
+    rho, u = inputs.taylor_green(n, n, 0.05)
+    solid, achieved, _ = inputs.porous_discs(n, n, 0.3, rmin=8, rmax=32)
+    big = [("taylor_green_%d" % n, dict(nx=n, ny=n, tau=0.8), rho, u, n * n, None, "dense"),
+           ("porous_phi%.2f_%d" % (achieved, n),
+            dict(nx=n, ny=n, tau=0.8, solid=solid, force=(1e-6, 0.0), periodic_y=False),
+            None, None, int((solid == 0).sum()), torch.as_tensor(solid == 0, device="cuda"), "sparse")]
+    del rho, u
+    res = {"steps_%d" % steps: _accuracy_runs(big, steps, ("f32", "f16s"), stream)}
+    small = []
+    for m in (1024, 2048, 4096):
+        r, v = inputs.taylor_green(m, m, 0.05)
+        small.append(("taylor_green_%d" % m, dict(nx=m, ny=m, tau=0.8), r, v, m * m, None, "dense"))
+        fx, r, v = inputs.poiseuille(m, m, 0.8, 0.05)
+        small.append(("poiseuille_%d" % m, dict(nx=m, ny=m, tau=0.8, force=(fx, 0.0), periodic_y=False),
+                      r, v, m * m, None, "dense"))
+    res["steps_1000"] = _accuracy_runs(small, 1000, ("f32", "f16s"), stream)
+    return {"sweep": "precision", "results": res}
 
 
 def main():

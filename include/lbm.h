@@ -53,8 +53,12 @@ typedef enum {
 } lbm_status;
 
 /* Storage of the distributions.  Every mode stores f_i - w_i ("shifted");
- * LBM_F16S rounds it to binary16 (round-to-nearest-even) and computes in
- * FP32, LBM_F32 stores and computes FP32, LBM_F64 stores and computes FP64. */
+ * LBM_F64 stores and computes FP64, LBM_F32 FP32.  LBM_F16S computes in FP32
+ * and stores (f_i - w_i) * 2^10 in binary16 (exact power-of-two scale;
+ * |f_i - w_i| <= 64); the time step rounds it stochastically with random
+ * bits that depend only on the node, the link and the step index, so runs
+ * are deterministic and identical across layouts and patterns; every other
+ * encode (init, set_f) rounds to nearest. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 } lbm_precision;
 
 /* LBM_DENSE: f[i][ny][nx].  LBM_SPARSE_TILE16: only 16x16 tiles that hold a
@@ -159,9 +163,11 @@ lbm_status lbm_load_state(lbm_ctx *ctx, const void *d_src);
 
 /* Forward recompute for the adjoint: runs n steps from native state
  * d_states[0] and writes A_{k+1} into d_states[k+1] (k = 0..n-1);
- * h_states is a HOST array of n+1 device pointers.  The context's own
- * lattice is not touched.  Two-lattice dense only. */
-lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n);
+ * h_states is a HOST array of n+1 device pointers; t0 is the step index of
+ * d_states[0] (FP16s stochastic rounding then reproduces the original run).
+ * The context's own lattice and step counter are not touched.  Two-lattice
+ * only. */
+lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long long t0);
 
 /* Discrete adjoint of n steps (transpose of the linearised Algorithm 1
  * step, with the bounce-back gather transposed into a push).

@@ -49,6 +49,7 @@ class LBMFunction(torch.autograd.Function):
             sim.set_f(f0.detach())
         sim.set_force(None if force is None else force.detach())
         segs = checkpoint_segments(T, K)
+        t_start = sim.steps
         ckpts = []
         for (_, n) in segs:
             ckpts.append(sim.save_state())
@@ -56,7 +57,7 @@ class LBMFunction(torch.autograd.Function):
         final = sim.save_state()
         rho, u = sim.macros()
         ctx.sim, ctx.T, ctx.K = sim, T, K
-        ctx.ckpts, ctx.final, ctx.segs = ckpts, final, segs
+        ctx.ckpts, ctx.final, ctx.segs, ctx.t_start = ckpts, final, segs, t_start
         ctx.has_f0, ctx.has_force = f0 is not None, force is not None
         return rho, u
 
@@ -73,10 +74,10 @@ class LBMFunction(torch.autograd.Function):
                             None if g_u is None else g_u.contiguous(), lam, gF)
         bufs = [sim.new_state() for _ in range(max(0, ctx.K - 1))]
         for s in range(len(ctx.segs) - 1, -1, -1):
-            _, n = ctx.segs[s]
+            start, n = ctx.segs[s]
             states = [ctx.ckpts[s]] + bufs[: n - 1]
             if n > 1:
-                sim.forward_states(states)
+                sim.forward_states(states, ctx.t_start + start)
             sim.backward(states, lam, lam_tmp, gF)
         sim.load_state(ctx.final)
         return (None, None, None, lam if ctx.has_f0 else None, gF if ctx.has_force else None)

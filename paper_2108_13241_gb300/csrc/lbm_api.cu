@@ -349,13 +349,13 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
         if (ctx->p.pattern == LBM_TWO_LATTICE) {
             const void *a = ctx->lat[ctx->cur];
             void *b = ctx->lat[1 - ctx->cur];
-            e = LBM_DISPATCH(ctx->p.precision,
-                             launch_step<P>(g, ctx->phys, MODE_TWO_LATTICE, a, b, ctx->stream));
+            e = LBM_DISPATCH(ctx->p.precision, launch_step<P>(g, ctx->phys, MODE_TWO_LATTICE, a, b,
+                                                              (unsigned long long)ctx->steps, ctx->stream));
             ctx->cur = 1 - ctx->cur;
         } else {
             const int mode = ctx->phase == PH_SWAPPED ? MODE_AA_PULLPUSH : MODE_AA_LOCAL;
-            e = LBM_DISPATCH(ctx->p.precision,
-                             launch_step<P>(g, ctx->phys, mode, ctx->lat[0], ctx->lat[0], ctx->stream));
+            e = LBM_DISPATCH(ctx->p.precision, launch_step<P>(g, ctx->phys, mode, ctx->lat[0], ctx->lat[0],
+                                                              (unsigned long long)ctx->steps, ctx->stream));
             ctx->phase = ctx->phase == PH_SWAPPED ? PH_STREAMED : PH_SWAPPED;
         }
         if (e != cudaSuccess) return cuda_check(ctx, e, "step kernel");
@@ -455,15 +455,16 @@ lbm_status lbm_load_state(lbm_ctx *ctx, const void *d_src) {
                                            ctx->stream), "load state");
 }
 
-lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n) {
+lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long long t0) {
     LBM_CTX_CHECK(ctx);
     if (ctx->p.pattern != LBM_TWO_LATTICE) return fail(ctx, LBM_ERR_UNSUPPORTED, "needs two-lattice");
     if (n < 0 || (n > 0 && !h_states)) return fail(ctx, LBM_ERR_INVALID, "bad state list");
     for (int k = 0; k < n; ++k) {
         if (!h_states[k] || !h_states[k + 1] || ((uintptr_t)h_states[k] & 15) || ((uintptr_t)h_states[k + 1] & 15))
             return fail(ctx, LBM_ERR_INVALID, "bad state pointer");
-        cudaError_t e = LBM_DISPATCH(ctx->p.precision, launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE,
-                                                                      h_states[k], h_states[k + 1], ctx->stream));
+        cudaError_t e = LBM_DISPATCH(ctx->p.precision,
+                                     launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE, h_states[k], h_states[k + 1],
+                                                    (unsigned long long)(t0 + k), ctx->stream));
         if (e != cudaSuccess) return cuda_check(ctx, e, "forward_states kernel");
     }
     return LBM_OK;

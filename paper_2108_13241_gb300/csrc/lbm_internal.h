@@ -63,8 +63,10 @@ struct Phys {
 
 // Launchers, defined in lbm_kernels.cuh and instantiated per precision P
 // (an lbm_precision value) in kern_f64.cu, kern_f32.cu, kern_f16s.cu.
+// t: index of the time step (random bits of FP16s stochastic rounding)
 template <int P> cudaError_t launch_step(const Geo &g, const Phys &ph, int mode,
-                                         const void *src, void *dst, cudaStream_t s);
+                                         const void *src, void *dst, unsigned long long t,
+                                         cudaStream_t s);
 template <int P> cudaError_t launch_init(const Geo &g, int phase, const void *rho,
                                          const void *u, void *lat, cudaStream_t s);
 template <int P> cudaError_t launch_set_f(const Geo &g, int phase, const void *f, void *lat,

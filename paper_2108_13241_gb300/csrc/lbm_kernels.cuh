@@ -48,27 +48,60 @@ template <class C> __host__ __device__ constexpr C wgt(int i) {
 // ------------------------------------------------------------- storage
 
 template <int P> struct St;
+// dec/enc convert between the stored element and f_i - w_i in the compute
+// type; enc_sr is the encode of the time step, given 32 random bits.
 template <> struct St<LBM_F64> {
     typedef double R; // stored element
     typedef double C; // compute type
-    enum { VEC = 2 };
+    enum { VEC = 2, STOCHASTIC = 0 };
     static __device__ __forceinline__ C dec(R r) { return r; }
     static __device__ __forceinline__ R enc(C c) { return c; }
+    static __device__ __forceinline__ R enc_sr(C c, unsigned) { return c; }
 };
 template <> struct St<LBM_F32> {
     typedef float R;
     typedef float C;
-    enum { VEC = 4 };
+    enum { VEC = 4, STOCHASTIC = 0 };
     static __device__ __forceinline__ C dec(R r) { return r; }
     static __device__ __forceinline__ R enc(C c) { return c; }
+    static __device__ __forceinline__ R enc_sr(C c, unsigned) { return c; }
 };
+// FP16s: binary16 bits of (f_i - w_i) * 2^10.  The power-of-two scale is
+// exact; it moves the small deviations of slow flows (|f_i - w_i| down to
+// 6e-8) into binary16's normal range while keeping |f_i - w_i| up to 64
+// finite.  The time step rounds stochastically (enc_sr): the 13 mantissa
+// bits that binary16 drops get 13 uniform random bits added before
+// truncation, so the rounding error has zero mean instead of repeating
+// itself step after step in a slowly varying flow; values below binary16's
+// normal range round to nearest.
 template <> struct St<LBM_F16S> {
-    typedef unsigned short R; // binary16 bits of f_i - w_i
+    typedef unsigned short R;
     typedef float C;
-    enum { VEC = 4 };          // 8-byte vectors: 4 nodes per thread
-    static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)); }
-    static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c)); }
+    enum { VEC = 4, STOCHASTIC = 1 }; // 8-byte vectors: 4 nodes per thread
+    static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)) * (1.0f / 1024.0f); }
+    static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c * 1024.0f)); }
+    static __device__ __forceinline__ R enc_sr(C c, unsigned rnd) {
+        const float v = c * 1024.0f;
+        const unsigned b = __float_as_uint(v);
+        const bool normal = (b & 0x7F800000u) >= (113u << 23); // |v| >= 2^-14
+        const __half h = normal ? __float2half_rz(__uint_as_float(b + (rnd >> 19))) : __float2half_rn(v);
+        return __half_as_ushort(h);
+    }
 };
+
+// Counter-based random bits for stochastic rounding: the 32-bit finaliser of
+// Appleby's MurmurHash3 applied to (node index, time step), then one
+// Numerical Recipes linear congruential step per link.  Deterministic, and
+// the same for a node, link and step in every layout and pattern.
+__device__ __forceinline__ unsigned fmix32(unsigned h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ unsigned lcg_next(unsigned h) { return h * 1664525u + 1013904223u; }
 
 // One aligned vector of VEC stored values: 16 bytes (FP64, FP32) or 8 bytes
 // (FP16s), moved with one load or store instruction.
@@ -234,21 +267,20 @@ template <int VEC> struct TileAddr {
         int nb[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
-            const int n = __ldg(g.nbr + 9 * (long long)t + j);
+            const int n = __ldg(g.nbr + 9 * t + j);
             nb[j] = n < 0 ? t : n; // absent: any valid tile, the value is unused
         }
 #pragma unroll
         for (int d = -1; d <= 1; ++d) {
             const int r = ly + d;
             const int oy = r < 0 ? -1 : (r >= TILE ? 1 : 0);
-            const int rr = (r & (TILE - 1)) * TILE;
-            const int tc = pick3(oy, nb[1], nb[4], nb[7]);
-            const int tl_ = pick3(oy, nb[0], nb[3], nb[6]);
-            const int tr_ = pick3(oy, nb[2], nb[5], nb[8]);
-            const unsigned base = (unsigned)tc * (9u * TILE_N) + (unsigned)rr;
+            const unsigned rr = (unsigned)((r & (TILE - 1)) * TILE);
+            const unsigned base = (unsigned)pick3(oy, nb[1], nb[4], nb[7]) * (9u * TILE_N) + rr;
             rowb[d + 1] = base + lx0;
-            lb[d + 1] = xv == 0 ? (unsigned)tl_ * (9u * TILE_N) + (unsigned)(rr + TILE - 1) : base + lx0 - 1;
-            rb[d + 1] = xv == TPR - 1 ? (unsigned)tr_ * (9u * TILE_N) + (unsigned)rr : base + lx0 + VEC;
+            lb[d + 1] = xv == 0 ? (unsigned)pick3(oy, nb[0], nb[3], nb[6]) * (9u * TILE_N) + rr + (TILE - 1)
+                                : base + lx0 - 1;
+            rb[d + 1] = xv == TPR - 1 ? (unsigned)pick3(oy, nb[2], nb[5], nb[8]) * (9u * TILE_N) + rr
+                                      : base + lx0 + VEC;
         }
     }
     __device__ __forceinline__ unsigned vidx(int slot, int dy) const {
@@ -422,7 +454,8 @@ __device__ __forceinline__ void adjoint_node(const C f[9], const C lam[9], C Fx,
 // thread's own vectors.
 template <class S, int MODE, class A>
 __device__ __forceinline__ void gather_raw(const A &ad, const typename S::R *src, bool active, int lane,
-                                           V16<typename S::R, S::VEC> raw[9], typename S::R edge[9]) {
+                                           unsigned long long mv, V16<typename S::R, S::VEC> raw[9],
+                                           typename S::R edge[9]) {
     typedef typename S::R R;
     constexpr int VEC = S::VEC;
     constexpr bool NC = (MODE == MODE_TWO_LATTICE);
@@ -435,35 +468,36 @@ __device__ __forceinline__ void gather_raw(const A &ad, const typename S::R *src
         edge[i] = R(0);
     }
     if constexpr (MODE == MODE_AA_LOCAL) return;
-    // A lane whose VEC nodes are all solid moves no vectors, but for the
-    // diagonal links its neighbour lane pulls one value through it from the
-    // row above or below, which may be fluid: load just that value.
-    if (!active && ad.valid) {
-#pragma unroll
-        for (int i = 5; i < 9; ++i) {
-            const int slot = (MODE == MODE_AA_PULLPUSH) ? opp(i) : i;
-            if (cx(i) == 1 && ad.right_in_warp(lane))
-                raw[i].v[VEC - 1] = ld1<NC>(src + ad.eidx(slot, VEC - 1, 0, -cy(i)));
-            if (cx(i) == -1 && ad.left_in_warp(lane))
-                raw[i].v[0] = ld1<NC>(src + ad.eidx(slot, 0, 0, -cy(i)));
-        }
-    }
+    // Neighbour lanes whose VEC nodes are all solid (inactive) load nothing.
+    // The values this lane pulls through them are then either solid (links
+    // along x: bounced) or in the row above/below (diagonals), which this
+    // lane loads itself unless its own mask bounces that link.
+    const bool lact = __shfl_up_sync(LBM_FULL, active ? 1 : 0, 1) != 0;
+    const bool ract = __shfl_down_sync(LBM_FULL, active ? 1 : 0, 1) != 0;
+    const bool lin = ad.left_in_warp(lane) && lact;
+    const bool rin = ad.right_in_warp(lane) && ract;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const int slot = (MODE == MODE_AA_PULLPUSH) ? opp(i) : i;
-        if (cx(i) == 1 && active && !ad.left_in_warp(lane))
-            edge[i] = ld1<NC>(src + ad.eidx(slot, 0, -1, -cy(i)));
-        if (cx(i) == -1 && active && !ad.right_in_warp(lane))
-            edge[i] = ld1<NC>(src + ad.eidx(slot, VEC - 1, 1, -cy(i)));
+        if (cx(i) == 1) {
+            const bool bounced = (mv >> (i - 1)) & 1ull; // node 0
+            if (active && !lin && !(ad.left_in_warp(lane) && cy(i) == 0) && !bounced)
+                edge[i] = ld1<NC>(src + ad.eidx(slot, 0, -1, -cy(i)));
+        }
+        if (cx(i) == -1) {
+            const bool bounced = (mv >> (8 * (VEC - 1) + i - 1)) & 1ull; // node VEC-1
+            if (active && !rin && !(ad.right_in_warp(lane) && cy(i) == 0) && !bounced)
+                edge[i] = ld1<NC>(src + ad.eidx(slot, VEC - 1, 1, -cy(i)));
+        }
     }
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         if (cx(i) == 1) {
             const R l = shfl_up1(raw[i].v[VEC - 1]);
-            if (ad.left_in_warp(lane)) edge[i] = l;
+            if (lin) edge[i] = l;
         } else if (cx(i) == -1) {
             const R r = shfl_down1(raw[i].v[0]);
-            if (ad.right_in_warp(lane)) edge[i] = r;
+            if (rin) edge[i] = r;
         }
     }
 }
@@ -581,7 +615,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
                                         const V16<typename S::R, S::VEC> own[9],
                                         unsigned long long mv, const V16<typename S::R, S::VEC> raw[9],
                                         const typename S::R edge[9], const typename S::C Fx[],
-                                        const typename S::C Fy[], const Coef<typename S::C> &co,
+                                        const typename S::C Fy[], const Coef<typename S::C> &co, unsigned tseed,
                                         V16<typename S::R, S::VEC> out[9]) {
     typedef typename S::C C;
     C f[9];
@@ -594,8 +628,17 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
     }
     if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, raw, own, K, m, f);
     collide<C, FORCE != FORCE_NONE>(f, Fx[K], Fy[K], co);
+    if constexpr (S::STOCHASTIC) {
+        unsigned h = fmix32((unsigned)ad.node(K) ^ tseed);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);
+        for (int i = 0; i < 9; ++i) {
+            h = lcg_next(h);
+            out[i].v[K] = S::enc_sr(f[i], h);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);
+    }
 }
 
 // Nodes K0 .. K1-1 of the thread, in order (compile-time unrolled).
@@ -607,10 +650,11 @@ struct NodeRange {
                                                const V16<typename S::R, S::VEC> raw[9],
                                                const typename S::R edge[9], const typename S::C Fx[],
                                                const typename S::C Fy[], const Coef<typename S::C> &co,
-                                               V16<typename S::R, S::VEC> out[9]) {
+                                               unsigned tseed, V16<typename S::R, S::VEC> out[9]) {
         if constexpr (K < K1) {
-            do_node<S, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, out);
-            NodeRange<S, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, out);
+            do_node<S, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, tseed, out);
+            NodeRange<S, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, tseed,
+                                                                   out);
         }
     }
 };
@@ -664,14 +708,14 @@ template <int P, bool HAS_MASK> struct MinBlocks {
 
 template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
 __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
-    k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0) {
+    k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0, unsigned step) {
     typedef StV<P, A::VEC_> S;
     typedef typename S::R R;
     typedef typename S::C C;
     constexpr int VEC = S::VEC;
     const R *src = reinterpret_cast<const R *>(src_v);
     R *dst = reinterpret_cast<R *>(dst_v);
-    const A ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + (int)blockIdx.y);
+    A ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + (int)blockIdx.y);
     const int lane = threadIdx.x & 31;
 
     unsigned long long mv = 0;
@@ -681,7 +725,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
 
     V16<R, VEC> raw[9];
     R edge[9];
-    gather_raw<S, MODE>(ad, src, active, lane, raw, edge);
+    gather_raw<S, MODE>(ad, src, active, lane, mv, raw, edge);
     if (!active) return; // no collective operation follows
     V16<R, VEC> own[9];
     if (HAS_MASK && MODE != MODE_AA_LOCAL && mv != 0ull) preload_own<S, MODE>(ad, src, mv, own);
@@ -691,7 +735,8 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
     const Coef<C> co(ph);
 
     V16<R, VEC> out[9];
-    NodeRange<S, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, out);
+    const unsigned tseed = S::STOCHASTIC ? fmix32(step * 0x9E3779B9u + 0x632BE5ABu) : 0u;
+    NodeRange<S, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, tseed, out);
     store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
 }
 
@@ -716,7 +761,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
     const C *lin = reinterpret_cast<const C *>(lam_in_v);
     C *lout = reinterpret_cast<C *>(lam_out_v);
     C *gF = reinterpret_cast<C *>(gF_v);
-    const DenseAddr<VEC> ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + (int)blockIdx.y);
+    DenseAddr<VEC> ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + (int)blockIdx.y);
     const int lane = threadIdx.x & 31;
     unsigned long long mv = 0;
     if (g.has_mask) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
@@ -725,7 +770,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
 
     V16<R, VEC> raw[9];
     R edge[9];
-    gather_raw<S, MODE_TWO_LATTICE>(ad, src, active, lane, raw, edge);
+    gather_raw<S, MODE_TWO_LATTICE>(ad, src, active, lane, mv, raw, edge);
     V16<R, VEC> own[9];
     if (mv != 0ull) preload_own<S, MODE_TWO_LATTICE>(ad, src, mv, own);
     C Fx[VEC], Fy[VEC];
@@ -1117,40 +1162,43 @@ template <int VEC> static Shape step_shape(const Geo &g) {
 }
 
 template <int P, class A, int MODE, bool HM, int F>
-static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, cudaStream_t s) {
+static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, cudaStream_t s) {
     const Shape sh = step_shape<A::VEC_>(g);
     if (sh.gx == 0) return cudaSuccess;
     for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
         const unsigned gy = sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u;
-        k_step<P, A, MODE, HM, F><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, (int)y0);
+        k_step<P, A, MODE, HM, F><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, (int)y0, t);
     }
     return cudaGetLastError();
 }
 template <int P, class A, int MODE, bool HM>
-static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, cudaStream_t s) {
+static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, cudaStream_t s) {
     switch (ph.force_mode) {
-    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, src, dst, s);
-    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, s);
-    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, src, dst, s);
+    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, src, dst, t, s);
+    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, t, s);
+    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, src, dst, t, s);
     }
 }
 template <int P, class A, bool HM>
-static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, cudaStream_t s) {
+static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned t,
+                             cudaStream_t s) {
     switch (mode) {
-    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, src, dst, s);
-    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, s);
-    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, src, dst, s);
+    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, src, dst, t, s);
+    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, t, s);
+    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, src, dst, t, s);
     }
 }
 
 template <int P>
-cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, cudaStream_t s) {
+cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned long long t,
+                        cudaStream_t s) {
     constexpr int VM = StepVec<P, true>::value, VN = StepVec<P, false>::value;
+    const unsigned tt = (unsigned)t;
     if (g.layout == LBM_DENSE) {
-        if (g.has_mask) return step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, s);
-        return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, s);
+        if (g.has_mask) return step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, tt, s);
+        return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, tt, s);
     }
-    return step_mode<P, TileAddr<VM>, true>(g, ph, mode, src, dst, s);
+    return step_mode<P, TileAddr<VM>, true>(g, ph, mode, src, dst, tt, s);
 }
 
 static inline unsigned node_blocks(const Geo &g) {
@@ -1213,7 +1261,8 @@ cudaError_t launch_macros_adjoint(const Geo &g, const Phys &ph, const void *stat
 }
 
 #define LBM_INSTANTIATE(P)                                                                                  \
-    template cudaError_t launch_step<P>(const Geo &, const Phys &, int, const void *, void *, cudaStream_t); \
+    template cudaError_t launch_step<P>(const Geo &, const Phys &, int, const void *, void *, unsigned long long, \
+                                        cudaStream_t);                                                      \
     template cudaError_t launch_init<P>(const Geo &, int, const void *, const void *, void *, cudaStream_t); \
     template cudaError_t launch_set_f<P>(const Geo &, int, const void *, void *, cudaStream_t);             \
     template cudaError_t launch_get_f<P>(const Geo &, int, const void *, void *, cudaStream_t);             \

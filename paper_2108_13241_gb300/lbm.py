@@ -85,7 +85,7 @@ def _load():
         "lbm_state_bytes": ([_vp, ctypes.POINTER(ctypes.c_size_t)], st),
         "lbm_save_state": ([_vp, _vp], st),
         "lbm_load_state": ([_vp, _vp], st),
-        "lbm_forward_states": ([_vp, ctypes.POINTER(_vp), ctypes.c_int], st),
+        "lbm_forward_states": ([_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_longlong], st),
         "lbm_backward": ([_vp, ctypes.POINTER(_vp), ctypes.c_int, _vp, _vp, _vp], st),
         "lbm_macros_backward": ([_vp, _vp, _vp, _vp, _vp], st),
         "lbm_link_mask": ([_vp, _vp], st),
@@ -213,10 +213,10 @@ def _ptr_array(ts: Sequence[torch.Tensor]):
     return arr
 
 
-def lbm_forward_states(ctx, states: Sequence[torch.Tensor]):
+def lbm_forward_states(ctx, states: Sequence[torch.Tensor], t0: int = 0):
     """states[0] holds A_t0; fills states[1..n] (n = len(states) - 1)."""
     _check("lbm_forward_states",
-           _load().lbm_forward_states(ctx, _ptr_array(states), len(states) - 1), ctx)
+           _load().lbm_forward_states(ctx, _ptr_array(states), len(states) - 1, int(t0)), ctx)
 
 
 def lbm_backward(ctx, states: Sequence[torch.Tensor], lam: torch.Tensor, lam_tmp: torch.Tensor,
@@ -435,8 +435,8 @@ class LBM:
     def load_state(self, src: torch.Tensor):
         lbm_load_state(self.ctx, src)
 
-    def forward_states(self, states: Sequence[torch.Tensor]):
-        lbm_forward_states(self.ctx, states)
+    def forward_states(self, states: Sequence[torch.Tensor], t0: int = 0):
+        lbm_forward_states(self.ctx, states, t0)
 
     def backward(self, states: Sequence[torch.Tensor], lam: torch.Tensor, lam_tmp: torch.Tensor,
                  grad_force: torch.Tensor):
