@@ -435,6 +435,57 @@ def extra_measurements(args):
     return out
 
 
+def porosity_sweep(n: int = 4096, steps: int = 300):
+    """Sparse computational efficiency eta_P (Eq. 9) over porosity, Sec. 4.2.2's
+    sweep: random discs r in [8, 256] (phi 0.1 .. 0.9), the regular 8 x 8 disc
+    array (phi 0.3 .. 0.9) and the r in [8, 32] discs of the porous workload
+    (phi 0.1 .. 0.9); FP32, two-lattice, periodic x, walls y, F = (1e-6, 0).
+    Each geometry runs in the tiled layout (only tiles with fluid stored) and
+    in the dense layout with the per-node link mask (the paper's bitmask-node
+    comparison); eta_P divides each by the same layout on the all-fluid box
+    with the same sides.  GLUPS count fluid nodes only."""
+    import torch
+    from paper_2108_13241_gb300 import inputs, lbm
+    stream = torch.cuda.current_stream()
+    peak, _ = peaks()
+    base = dict(nx=n, ny=n, tau=0.8, force=(1e-6, 0.0), periodic_y=False)
+
+    def glups(solid, layout):
+        sim = lbm.LBM(precision="f32", layout=layout, pattern="two_lattice", solid=solid, **base)
+        nf = sim.fluid_nodes
+        sim.init_equilibrium(None, None)
+        t = time_steps(sim, steps, 10, stream)
+        tiles = sim.tile_map()[1].shape[0] if layout == "sparse" else None
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        return nf * steps / t / 1e9, nf, tiles
+
+    ref = {lay: glups(None, lay)[0] for lay in ("sparse", "dense")}
+    res = {"all_fluid": {lay: round(g, 3) for lay, g in ref.items()}}
+    gens = [("random_r8_256", [round(0.1 * k, 1) for k in range(1, 10)],
+             lambda phi: inputs.porous_discs(n, n, phi, rmin=8, rmax=256)[:2]),
+            ("array_8x8", [round(0.1 * k, 1) for k in range(3, 10)],
+             lambda phi: inputs.circle_array(n, n, phi, 8)[:2]),
+            ("random_r8_32", [round(0.1 * k, 1) for k in range(1, 10)],
+             lambda phi: inputs.porous_discs(n, n, phi, rmin=8, rmax=32)[:2])]
+    for name, phis, gen in gens:
+        rows = []
+        for phi in phis:
+            solid, achieved = gen(phi)
+            row = {"phi": round(achieved, 4)}
+            for lay in ("sparse", "dense"):
+                g, nf, tiles = glups(solid, lay)
+                row[lay] = {"GLUPS": round(g, 3), "eta_P": round(g / ref[lay], 3),
+                            "frac_of_measured_hbm": round(g * node_bytes("f32") / peak, 4)}
+                if tiles is not None:
+                    row["kept_tiles"] = int(tiles)
+            row["fluid_nodes"] = int(nf)
+            rows.append(row)
+        res[name] = rows
+    return {"sweep": "porosity", "n": n, "steps": steps, "precision": "f32", "results": res}
+
+
 def adjoint_cost():
     """Cost of one adjoint step relative to one forward step on the
     differentiable channel (512 x 256, 12 cylinders, FP32, T = 2000,
@@ -555,12 +606,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="run the 8192^2 FP64/FP32/FP16s precision sweep instead of the benchmark")
+    ap.add_argument("--porosity-sweep", action="store_true",
+                    help="run the 4096^2 eta_P sweep over porosity instead of the benchmark")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.sweep:
+    if args.sweep or args.porosity_sweep:
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps(precision_sweep()), flush=True)
+        print(json.dumps(precision_sweep() if args.sweep else porosity_sweep()), flush=True)
         return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -263,6 +263,13 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     ph.fy_f = (float)ph.fy;
     for (int s = 0; s < WALL_SIDES; ++s)
         for (int i = 0; i < 9; ++i) ph.wt_f[s][i] = (float)ph.wt[s][i];
+    ph.kq[0] = ph.omega / 3.0;
+    ph.kq[1] = ph.omega / 12.0;
+    for (int q = 0; q < 2; ++q) {
+        const double k = (double)ph.omega_f / (q == 0 ? 3.0 : 12.0);
+        ph.kq_hi[q] = (float)k;
+        ph.kq_lo[q] = (float)(k - (double)ph.kq_hi[q]);
+    }
     set_force_mode(c);
 
     lbm_status st = LBM_OK;

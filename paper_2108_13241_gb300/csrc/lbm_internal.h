@@ -59,6 +59,10 @@ struct Phys {
     // the same constants rounded to FP32 on the host (FP32 / FP16s kernels)
     float omega_f, om1_f, kk_f, fx_f, fy_f;
     float wt_f[WALL_SIDES][9];
+    // omega/3 and omega/12 (3 omega w for axis and diagonal links): FP64, and
+    // for FP32 the float pair (hi + lo) of omega_f/3, omega_f/12
+    double kq[2];
+    float kq_hi[2], kq_lo[2];
 };
 
 // Launchers, defined in lbm_kernels.cuh and instantiated per precision P

@@ -339,38 +339,88 @@ template <> struct PC<float> {
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
-// Moments of the gathered shifted f' (Eq. 2; u shifted by F/2).
-template <class C, bool HAS_F>
-__device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rho, C &inv, C &ux,
-                                        C &uy) {
+// Rounded-to-nearest arithmetic the compiler may not contract or reorder,
+// for the error-free transformations below.
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// Knuth's TwoSum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = rn_add(a, b);
+    const float bb = rn_sub(s, a);
+    e = rn_add(rn_sub(a, rn_sub(s, bb)), rn_sub(b, bb));
+}
+
+// Moments of the gathered shifted f' (Eq. 2; u shifted by F/2), and the
+// momentum j = m + F/2 = rho u.  COMP: j is returned as jx + jxl exactly
+// (TwoSum), because F/2 is often below half an ulp of m and rounding it away
+// would bias the momentum gain the same way every step.
+template <class C, bool HAS_F, bool COMP = false>
+__device__ __forceinline__ void moments_j(const C f[9], C Fx, C Fy, C &drho, C &rho, C &inv, C &ux, C &uy,
+                                          C &jx, C &jy, C &jxl, C &jyl) {
     drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     rho = C(1) + drho;
     const C mx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const C my = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
     inv = recip(rho);
+    jxl = jyl = C(0);
     if (HAS_F) {
-        ux = (mx + C(0.5) * Fx) * inv;
-        uy = (my + C(0.5) * Fy) * inv;
+        if constexpr (COMP) {
+            two_sum(mx, C(0.5) * Fx, jx, jxl);
+            two_sum(my, C(0.5) * Fy, jy, jyl);
+        } else {
+            jx = mx + C(0.5) * Fx;
+            jy = my + C(0.5) * Fy;
+        }
     } else {
-        ux = mx * inv;
-        uy = my * inv;
+        jx = mx;
+        jy = my;
     }
+    ux = jx * inv;
+    uy = jy * inv;
+}
+template <class C, bool HAS_F>
+__device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rho, C &inv, C &ux,
+                                        C &uy) {
+    C jx, jy, jxl, jyl;
+    moments_j<C, HAS_F>(f, Fx, Fy, drho, rho, inv, ux, uy, jx, jy, jxl, jyl);
 }
 
 template <class C> struct Coef {
     C om, om1, kk;
+    C kh[2], kl[2]; // omega/3, omega/12 (axis, diagonal); kl: low part (FP32)
     __device__ __forceinline__ explicit Coef(const Phys &ph)
-        : om(PC<C>::omega(ph)), om1(PC<C>::om1(ph)), kk(PC<C>::kk(ph)) {}
+        : om(PC<C>::omega(ph)), om1(PC<C>::om1(ph)), kk(PC<C>::kk(ph)) {
+        if constexpr (sizeof(C) == 8) {
+            kh[0] = C(ph.kq[0]);
+            kh[1] = C(ph.kq[1]);
+            kl[0] = kl[1] = C(0);
+        } else {
+            kh[0] = C(ph.kq_hi[0]);
+            kh[1] = C(ph.kq_hi[1]);
+            kl[0] = C(ph.kq_lo[0]);
+            kl[1] = C(ph.kq_lo[1]);
+        }
+    }
 };
 
 // BGK relaxation with Guo source, in shifted variables, in place on f:
 //   f_i <- f_i + omega (f^eq_i - w_i - f_i) + S_i
 // evaluated pairwise over opposite links (c_opp = -c): the even part of
-// f^eq - w and S is shared, the odd part changes sign.
-template <class C, bool HAS_F>
+// f^eq - w and S is shared, the odd part changes sign.  The odd part of
+// omega f^eq is built from the momentum itself, 3 omega w_i (c_i . j) with
+// j = rho u = m + F/2, so that its momentum is omega j by construction.
+// COMP (FP32 storage): 3 omega w_i is carried as a float pair and the product
+// is formed error-free, because a constant rounded to FP32 would scale the
+// equilibrium momentum of every node by the same (1 + eps) each step -- a
+// bias that grows linearly with the step count in slowly varying flows.
+// FP16s storage rounding (2^-21 relative to w_i) dwarfs that bias, so its
+// kernels keep the cheaper form 3 omega w_i rho (c_i . u).
+template <class C, bool HAS_F, bool COMP>
 __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
-    C drho, rho, inv, ux, uy;
-    moments<C, HAS_F>(f, Fx, Fy, drho, rho, inv, ux, uy);
+    C drho, rho, inv, ux, uy, jx, jy, jxl, jyl;
+    moments_j<C, HAS_F, COMP>(f, Fx, Fy, drho, rho, inv, ux, uy, jx, jy, jxl, jyl);
     const C usq = C(1.5) * (ux * ux + uy * uy);
     const C om = co.om, om1 = co.om1;
     // omega * w_q * rho and omega * w_q * drho per weight class
@@ -389,23 +439,50 @@ __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
         if (HAS_F) G = G + K0 * (C(-3) * uF);
         f[0] = om1 * f[0] + G;
     }
-#define LBM_PAIR(I, J, T, CF, RQ, EQ, KQ)                                     \
-    {                                                                         \
-        const C t = (T);                                                      \
-        C P = EQ + RQ * (C(4.5) * (t * t) - usq);                             \
-        C Q = (C(3) * RQ) * t;                                                \
-        if (HAS_F) {                                                          \
-            const C cf = (CF);                                                \
-            P = P + KQ * (C(9) * (t * cf) - C(3) * uF);                       \
-            Q = Q + (C(3) * KQ) * cf;                                         \
-        }                                                                     \
-        f[I] = om1 * f[I] + (P + Q);                                          \
-        f[J] = om1 * f[J] + (P - Q);                                          \
+    // one pair of opposite links: T = c_i . u, S = c_i . j (SL: its low part),
+    // CF = c_i . F, weight class Q (0 axis, 1 diagonal)
+#define LBM_PAIR(I, J, T, SH, SL, CF, RQ, EQ, KQ, Q)                                        \
+    {                                                                                       \
+        const C t = (T);                                                                    \
+        C P = EQ + RQ * (C(4.5) * (t * t) - usq);                                           \
+        C qh, ql = C(0);                                                                    \
+        if constexpr (COMP) {                                                               \
+            qh = rn_mul(co.kh[Q], (SH));                                                    \
+            ql = rn_add(rn_fma(co.kh[Q], (SH), -qh), rn_fma(co.kh[Q], (SL), rn_mul(co.kl[Q], (SH)))); \
+        } else if constexpr (sizeof(C) == 8) {                                              \
+            qh = co.kh[Q] * (SH);                                                           \
+        } else {                                                                            \
+            qh = (C(3) * RQ) * t;                                                           \
+        }                                                                                   \
+        if (HAS_F) {                                                                        \
+            const C cf = (CF);                                                              \
+            P = P + KQ * (C(9) * (t * cf) - C(3) * uF);                                     \
+            ql = ql + (C(3) * KQ) * cf;                                                     \
+        }                                                                                   \
+        C gp, gm;                                                                           \
+        if constexpr (COMP) {                                                               \
+            gp = rn_add(rn_add(P, qh), ql);                                                 \
+            gm = rn_sub(rn_sub(P, qh), ql);                                                 \
+        } else {                                                                            \
+            gp = (P + qh) + ql;                                                             \
+            gm = (P - qh) - ql;                                                             \
+        }                                                                                   \
+        f[I] = om1 * f[I] + gp;                                                             \
+        f[J] = om1 * f[J] + gm;                                                             \
     }
-    LBM_PAIR(1, 3, ux, Fx, Ra, Ea, Ka)
-    LBM_PAIR(2, 4, uy, Fy, Ra, Ea, Ka)
-    LBM_PAIR(5, 7, ux + uy, Fx + Fy, Rd, Ed, Kd)
-    LBM_PAIR(6, 8, uy - ux, Fy - Fx, Rd, Ed, Kd)
+    C sd1h = jx + jy, sd1l = C(0), sd2h = jy - jx, sd2l = C(0);
+    if constexpr (COMP) {
+        two_sum(jx, jy, sd1h, sd1l);
+        two_sum(jy, -jx, sd2h, sd2l);
+        if (HAS_F) {
+            sd1l = sd1l + (jxl + jyl);
+            sd2l = sd2l + (jyl - jxl);
+        }
+    }
+    LBM_PAIR(1, 3, ux, jx, jxl, Fx, Ra, Ea, Ka, 0)
+    LBM_PAIR(2, 4, uy, jy, jyl, Fy, Ra, Ea, Ka, 0)
+    LBM_PAIR(5, 7, ux + uy, sd1h, sd1l, Fx + Fy, Rd, Ed, Kd, 1)
+    LBM_PAIR(6, 8, uy - ux, sd2h, sd2l, Fy - Fx, Rd, Ed, Kd, 1)
 #undef LBM_PAIR
 }
 
@@ -627,7 +704,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
         return;
     }
     if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, raw, own, K, m, f);
-    collide<C, FORCE != FORCE_NONE>(f, Fx[K], Fy[K], co);
+    collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC)>(f, Fx[K], Fy[K], co);
     if constexpr (S::STOCHASTIC) {
         unsigned h = fmix32((unsigned)ad.node(K) ^ tseed);
 #pragma unroll

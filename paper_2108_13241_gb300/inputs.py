@@ -149,6 +149,31 @@ def porous_discs(nx: int, ny: int, porosity: float, rmin: float = 8.0, rmax: flo
     return solid, 1.0 - nsolid / float(nx * ny), len(discs)
 
 
+def circle_array(nx: int, ny: int, porosity: float, m: int = 8):
+    """Regular m x m array of equal solid discs (Sec. 4.2.2's regular
+    arrangement): centres at ((k + 1/2) nx/m, (l + 1/2) ny/m), membership
+    (i - cx)^2 + (j - cy)^2 <= r^2 on the integer grid, r the smallest radius
+    (found by bisection on the node count) whose solid fraction reaches
+    1 - porosity.  Discs do not touch for porosity > 1 - pi/4 on a square
+    grid; lower porosities are rejected, as the paper leaves them out.
+
+    Returns (solid uint8[ny, nx], achieved porosity, r)."""
+    sx, sy = nx / m, ny / m
+    if porosity <= 1.0 - math.pi / 4.0 * min(sx, sy) ** 2 / (sx * sy) or porosity >= 1.0:
+        raise ValueError("porosity out of range for a non-touching %dx%d array" % (m, m))
+    target = int(round((1.0 - porosity) * nx * ny))
+    y = np.arange(ny)[:, None]
+    x = np.arange(nx)[None, :]
+    # distance^2 of every node to the centre of its own cell
+    dx = x - (np.floor(x / sx) + 0.5) * sx
+    dy = y - (np.floor(y / sy) + 0.5) * sy
+    d2 = dx * dx + dy * dy
+    vals = np.sort(d2.ravel())
+    r2 = vals[target - 1] if target > 0 else -1.0
+    solid = (d2 <= r2).astype(np.uint8)
+    return solid, 1.0 - int(solid.sum()) / float(nx * ny), math.sqrt(max(r2, 0.0))
+
+
 def channel_cylinders(nx: int, ny: int, count: int = 12, rmin: float = 6.0, rmax: float = 12.0,
                       clearance: float = 2.0, seed: int = GEOMETRY_SEED):
     """`count` non-overlapping discs in a channel periodic in x, walls in y.
