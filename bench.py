@@ -58,10 +58,17 @@ def peaks():
 
 
 def kernel_hash() -> str:
-    """Hash of the kernel source with comments and white space removed, so
-    that a profile stays valid across comment-only edits."""
+    """Hash of the step kernel's source -- every section of the kernel file
+    before the adjoint kernel, and the step launchers -- with comments and
+    white space removed, so that a profile of the step kernel stays valid
+    across comment-only edits and edits of the other kernels."""
     with open(KERNEL_SOURCE) as fh:
-        text = fh.read()
+        full = fh.read()
+    rule = "// " + "-" * 61 + " "
+    text = full[:full.index(rule + "adjoint kernel")]
+    launch = full.index(rule + "launchers")
+    end = full.rfind("\n", launch, full.index(" node_blocks(const Geo", launch))
+    text += full[launch:end]
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     text = re.sub(r"//[^\n]*", "", text)
     text = re.sub(r"\s+", "", text)
