@@ -19,6 +19,9 @@
  *                        (body in step_body.inc);
  *   orc_macros           Eq. 2 on the gathered f', F/2 shift of the
  *                        Guo forcing;
+ *   open sides           constant velocity / constant pressure (Sec. 3,
+ *                        after Zou & He 1997), in the gather of the step
+ *                        and the macros (orc_open_side, step_body.inc);
  *   orc_adjoint_step     discrete adjoint (transpose of the linearisation) of
  *                        orc_step;
  *   orc_macros_adjoint   transpose of orc_macros.
@@ -168,6 +171,18 @@ void orc_run(const orc_params *p, const uint8_t *mask, const double *force,
     if (a != A) memcpy(A, a, sizeof(double) * 9 * N);
 }
 
+static int orc_has_open(const orc_params *p)
+{
+    for (int s = 0; s < 4; ++s)
+        if (p->open_kind[s] != ORC_OPEN_NONE) return 1;
+    return 0;
+}
+
+static void orc_fill_nan(double *a, long n)
+{
+    for (long k = 0; k < n; ++k) a[k] = NAN;
+}
+
 /* Shared by the macros and the adjoints: the gather of step 1 at node (x, y),
  * also reporting for each link whether it bounced and, if not, its source. */
 static void orc_gather(const orc_params *p, const uint8_t *mask, const double *A,
@@ -205,6 +220,8 @@ void orc_macros(const orc_params *p, const uint8_t *mask, const double *force,
             int bounced[9];
             long src[9];
             orc_gather(p, mask, A, x, y, f, bounced, src);
+            for (int s = 0; s < 4; ++s)
+                if (p->open_kind[s] != ORC_OPEN_NONE) orc_open_side(p, s, x, y, f);
             double r = 0, mx = 0, my = 0;
             for (int i = 0; i < 9; ++i) {
                 r += f[i];
@@ -246,6 +263,7 @@ void orc_adjoint_step(const orc_params *p, const uint8_t *mask,
     const long N = (long)p->nx * p->ny;
     const double omega = 1.0 / p->tau;
     const double k = 1.0 - 0.5 * omega;
+    if (orc_has_open(p)) { orc_fill_nan(lam, 9 * N); return; }
     memset(lam, 0, sizeof(double) * 9 * N);
     for (int y = 0; y < p->ny; ++y) {
         for (int x = 0; x < p->nx; ++x) {
@@ -313,6 +331,7 @@ void orc_macros_adjoint(const orc_params *p, const uint8_t *mask,
                         const double *g_uy, double *lam, double *grad_force)
 {
     const long N = (long)p->nx * p->ny;
+    if (orc_has_open(p)) { orc_fill_nan(lam, 9 * N); return; }
     for (int y = 0; y < p->ny; ++y) {
         for (int x = 0; x < p->nx; ++x) {
             const long n = (long)y * p->nx + x;

@@ -21,8 +21,21 @@
 #include <stdint.h>
 
 /* Geometry and physics of one run.  A side is a half-way bounce-back wall
- * moving at (wall_ux[s], wall_uy[s]) unless its axis is periodic.
- * Sides: 0 west (x<0), 1 east (x>=nx), 2 south (y<0), 3 north (y>=ny). */
+ * moving at (wall_ux[s], wall_uy[s]) unless its axis is periodic or it is
+ * open.  Sides: 0 west (x<0), 1 east (x>=nx), 2 south (y<0), 3 north (y>=ny).
+ *
+ * Open sides (the paper's constant-velocity and constant-pressure boundary
+ * conditions after Zou & He, Sec. 3): the nodes of the outermost row or
+ * column are boundary nodes; the links that would pull from beyond the side
+ * get the values for which the node has the side's velocity (open_kind
+ * ORC_OPEN_VELOCITY: open_ux, open_uy) or density (ORC_OPEN_PRESSURE:
+ * open_rho, zero tangential velocity).  open_val[s], when not NULL, gives the
+ * values node by node along the side instead: velocity [2][len] (all u_x,
+ * then all u_y), pressure [len]; len = ny on west/east (index y), nx on
+ * south/north (index x). */
+#define ORC_OPEN_NONE 0
+#define ORC_OPEN_VELOCITY 1
+#define ORC_OPEN_PRESSURE 2
 typedef struct {
     int nx, ny;
     int periodic_x, periodic_y;
@@ -30,6 +43,9 @@ typedef struct {
     double tau;          /* BGK relaxation time, omega = 1/tau        */
     double fx, fy;       /* uniform body-force density (no field given) */
     double rho_w;        /* wall density in the moving-wall term       */
+    int open_kind[4];
+    double open_ux[4], open_uy[4], open_rho[4];
+    const double *open_val[4];
 } orc_params;
 
 /* Per-node link mask value of a node that takes no part in the update. */
@@ -48,6 +64,8 @@ void orc_run(const orc_params *p, const uint8_t *mask, const double *force,
              double *A, double *B, int nsteps);
 void orc_macros(const orc_params *p, const uint8_t *mask, const double *force,
                 const double *A, double *rho, double *ux, double *uy);
+/* The adjoints are those of steps without open sides; with an open side
+ * they write NaN to lam. */
 void orc_adjoint_step(const orc_params *p, const uint8_t *mask,
                       const double *force, const double *A,
                       const double *lam_next, double *lam, double *grad_force);

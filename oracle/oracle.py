@@ -60,7 +60,14 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("fx", ctypes.c_double), ("fy", ctypes.c_double),
         ("rho_w", ctypes.c_double),
+        ("open_kind", ctypes.c_int * 4),
+        ("open_ux", ctypes.c_double * 4), ("open_uy", ctypes.c_double * 4),
+        ("open_rho", ctypes.c_double * 4),
+        ("open_val", ctypes.c_void_p * 4),
     ]
+
+OPEN_NONE, OPEN_VELOCITY, OPEN_PRESSURE = 0, 1, 2
+SIDES = ("west", "east", "south", "north")
 
 
 @dataclass
@@ -74,6 +81,10 @@ class Setup:
     # wall velocities per side: west, east, south, north
     wall_u: list = field(default_factory=lambda: [(0.0, 0.0)] * 4)
     force: tuple = (0.0, 0.0)
+    # open sides: {side index: ("velocity", (ux, uy)) | ("pressure", rho)};
+    # the value may also be a per-node array along the side (velocity
+    # [2, len], pressure [len])
+    open: dict = field(default_factory=dict)
 
     def c(self) -> Params:
         p = Params()
@@ -84,6 +95,21 @@ class Setup:
         p.tau = self.tau
         p.fx, p.fy = self.force
         p.rho_w = 1.0
+        self._keep = []
+        for s, (kind, val) in self.open.items():
+            length = self.ny if s < 2 else self.nx
+            p.open_kind[s] = OPEN_VELOCITY if kind == "velocity" else OPEN_PRESSURE
+            arr = np.asarray(val, dtype=np.float64)
+            if kind == "velocity" and arr.shape == (2,):
+                p.open_ux[s], p.open_uy[s] = float(arr[0]), float(arr[1])
+            elif kind == "pressure" and arr.shape == ():
+                p.open_rho[s] = float(arr)
+            else:
+                want = (2, length) if kind == "velocity" else (length,)
+                assert arr.shape == want, (arr.shape, want)
+                arr = np.ascontiguousarray(arr)
+                self._keep.append(arr)
+                p.open_val[s] = arr.ctypes.data
         return p
 
 
