@@ -71,14 +71,36 @@ typedef enum { LBM_DENSE = 0, LBM_SPARSE_TILE16 = 1 } lbm_layout;
  * single-copy scheme the paper cites in Sec. 3). */
 typedef enum { LBM_TWO_LATTICE = 0, LBM_AA = 1 } lbm_pattern;
 
+/* Kind of a non-periodic side: a half-way bounce-back wall, or an open side
+ * with constant velocity or constant pressure (the boundary conditions after
+ * Zou & He that the paper lists in Sec. 3). */
+typedef enum { LBM_SIDE_WALL = 0, LBM_SIDE_VELOCITY = 1, LBM_SIDE_PRESSURE = 2 } lbm_side_kind;
+
 /* A domain side.  periodic != 0: the axis wraps (both sides of an axis must
- * agree).  periodic == 0: half-way bounce-back wall half a spacing outside
- * the outermost nodes, moving at (ux, uy); a link that crosses it gets the
- * term 6 w_i rho_0 (c_i . u_w), rho_0 = 1.  A link that leaves the domain
- * across two sides is decided by the south/north side first. */
+ * agree; kind must be 0).  periodic == 0 and kind == LBM_SIDE_WALL:
+ * half-way bounce-back wall half a spacing outside the outermost nodes,
+ * moving at (ux, uy); a link that crosses it gets the term
+ * 6 w_i rho_0 (c_i . u_w), rho_0 = 1.  A link that leaves the domain across
+ * two sides is decided by the south/north side first.
+ *
+ * Open sides (periodic == 0, kind != 0): the outermost row or column of
+ * nodes are boundary nodes.  Each link of a boundary node that would pull
+ * from beyond the side takes the value for which the node has velocity
+ * (ux, uy) (LBM_SIDE_VELOCITY; |u . n| < 1 for the outward normal n) or
+ * density rho > 0 with zero tangential velocity (LBM_SIDE_PRESSURE):
+ *   f_i = f_opp(i) + 6 w_i rho (c_i . u) - (c_i . t) N_t,
+ *   N_t = 1/2 sum_{c.n=0} (c_j . t) f_j - rho (u . t)/3,
+ *   rho (1 + u . n) = sum_{c.n=0} f_j + 2 sum_{c.n>0} f_j,
+ * t the tangent along the side (Zou & He 1997 for every side).  Corner links
+ * that also cross a wall follow the wall.  Two adjacent sides cannot both be
+ * open.  Open sides work with every precision, layout and pattern; the
+ * adjoint calls (lbm_backward, lbm_macros_backward) return
+ * LBM_ERR_UNSUPPORTED for them.  lbm_set_side_values gives per-node values. */
 typedef struct {
     int periodic;
-    double ux, uy;
+    double ux, uy;   /* wall velocity, or the velocity of a velocity side */
+    int kind;        /* lbm_side_kind */
+    double rho;      /* density of a pressure side */
 } lbm_side;
 
 typedef struct {
@@ -116,6 +138,15 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
 
 /* Frees the host context.  The workspace stays the caller's. */
 lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Per-node values of open side `side` (0 west, 1 east, 2 south, 3 north),
+ * compute type, along the side (index y on west/east, x on south/north):
+ * velocity side [2][len] (all u_x, then all u_y), pressure side [len]
+ * densities; len = ny on west/east, nx on south/north.  NULL returns to the
+ * uniform value of the parameters.  The pointer is kept, not copied, and
+ * read by every later step and lbm_macros.  LBM_ERR_INVALID if the side is
+ * not open or the pointer is not aligned to the compute type. */
+lbm_status lbm_set_side_values(lbm_ctx *ctx, int side, const void *d_values);
 
 /* Per-node body force F[2][ny][nx] (compute type), used by every later step,
  * macros and adjoint instead of (fx, fy); NULL returns to the uniform force.

@@ -66,8 +66,19 @@ const char *check_params(const lbm_params *p) {
     if (p->layout == LBM_SPARSE_TILE16 && p->south.periodic && p->ny % 16)
         return "sparse layout with a periodic y axis needs ny % 16 == 0";
     const lbm_side *s[4] = {&p->west, &p->east, &p->south, &p->north};
-    for (int k = 0; k < 4; ++k)
-        if (!std::isfinite(s[k]->ux) || !std::isfinite(s[k]->uy)) return "wall velocity must be finite";
+    const int nrm[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    for (int k = 0; k < 4; ++k) {
+        if (!std::isfinite(s[k]->ux) || !std::isfinite(s[k]->uy)) return "side velocity must be finite";
+        if (s[k]->kind < LBM_SIDE_WALL || s[k]->kind > LBM_SIDE_PRESSURE) return "unknown side kind";
+        if (s[k]->periodic && s[k]->kind != LBM_SIDE_WALL) return "a periodic side cannot be open";
+        if (s[k]->kind == LBM_SIDE_PRESSURE && !(s[k]->rho > 0.0 && std::isfinite(s[k]->rho)))
+            return "pressure side needs a finite density > 0";
+        if (s[k]->kind == LBM_SIDE_VELOCITY && !(std::fabs(s[k]->ux * nrm[k][0] + s[k]->uy * nrm[k][1]) < 1.0))
+            return "velocity side needs |u.n| < 1";
+    }
+    const bool open_x = s[0]->kind != LBM_SIDE_WALL || s[1]->kind != LBM_SIDE_WALL;
+    const bool open_y = s[2]->kind != LBM_SIDE_WALL || s[3]->kind != LBM_SIDE_WALL;
+    if (open_x && open_y) return "two adjacent sides cannot both be open";
     return nullptr;
 }
 
@@ -76,13 +87,13 @@ struct Plan {
     int ntiles, ntx, nty;
     bool has_mask;
     long long nslot;
-    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, total;
+    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_open, total;
     size_t lat_bytes, mask_bytes;
 };
 
 // Geometry tables and the workspace layout for p.
 void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int32_t> &tile_id,
-               std::vector<int32_t> &nbr, std::vector<int32_t> &txy, Plan &pl) {
+               std::vector<int32_t> &nbr, std::vector<int32_t> &txy, std::vector<int4> &open, Plan &pl) {
     const long long N = (long long)p.nx * p.ny;
     mask.assign((size_t)N, 0);
     pl.nfluid = build_link_mask(p, mask.data());
@@ -122,6 +133,9 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
     off += align256((size_t)RED_BLOCKS * 4 * sizeof(double));
     pl.off_out = off;
     off += align256(4 * sizeof(double));
+    build_open_nodes(p, mask.data(), open);
+    pl.off_open = off;
+    off += align256(open.size() * sizeof(int4));
     pl.total = off;
 }
 
@@ -183,8 +197,9 @@ lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes) {
     if (!bytes || check_params(p)) return LBM_ERR_INVALID;
     std::vector<uint8_t> mask;
     std::vector<int32_t> tid, nbr, txy;
+    std::vector<int4> open;
     Plan pl;
-    make_plan(*p, mask, tid, nbr, txy, pl);
+    make_plan(*p, mask, tid, nbr, txy, open, pl);
     if (9ll * pl.nslot >= (1ll << 32)) return LBM_ERR_INVALID;
     *bytes = pl.total;
     return LBM_OK;
@@ -201,8 +216,9 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     c->stream = (cudaStream_t)p->stream;
     c->sticky = LBM_OK;
     std::vector<int32_t> txy;
+    std::vector<int4> open;
     Plan pl;
-    make_plan(*p, c->mask, c->tile_id, c->nbr, txy, pl);
+    make_plan(*p, c->mask, c->tile_id, c->nbr, txy, open, pl);
     if (9ll * pl.nslot >= (1ll << 32)) {
         delete c;
         return LBM_ERR_INVALID;
@@ -237,7 +253,15 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     g.nslot = pl.nslot;
     g.nnode = (long long)p->nx * p->ny;
     g.has_mask = pl.has_mask;
+    if (p->layout == LBM_DENSE && pl.has_mask && p->ny >= 3) {
+        bool inner_free = true;
+        for (size_t n = (size_t)p->nx; n < (size_t)p->nx * (size_t)(p->ny - 1) && inner_free; ++n)
+            inner_free = c->mask[n] == 0;
+        g.frame_y = inner_free;
+    }
     g.mask = pl.mask_bytes ? reinterpret_cast<const uint8_t *>(ws + pl.off_mask) : nullptr;
+    g.nopen = (int)open.size();
+    g.open_nodes = open.empty() ? nullptr : reinterpret_cast<const int4 *>(ws + pl.off_open);
 
     Phys &ph = c->phys;
     std::memset(&ph, 0, sizeof(ph));
@@ -247,12 +271,22 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     const lbm_side *sides[4] = {&p->west, &p->east, &p->south, &p->north};
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 4; ++s) {
+        const bool wall = !sides[s]->periodic && sides[s]->kind == LBM_SIDE_WALL;
         for (int i = 0; i < 9; ++i) {
             // half-way bounce-back on a wall moving at u_w, rho_w = rho_0 = 1
-            ph.wt[s][i] = sides[s]->periodic ? 0.0 : 6.0 * W[i] * (CX[i] * sides[s]->ux + CY[i] * sides[s]->uy);
+            ph.wt[s][i] = wall ? 6.0 * W[i] * (CX[i] * sides[s]->ux + CY[i] * sides[s]->uy) : 0.0;
             if (ph.wt[s][i] != 0.0) ph.has_wall = 1;
         }
+        ph.open_kind[s] = sides[s]->periodic ? LBM_SIDE_WALL : sides[s]->kind;
+        if (ph.open_kind[s] != LBM_SIDE_WALL) ph.has_open = 1;
+        ph.open_u[s][0] = sides[s]->ux;
+        ph.open_u[s][1] = sides[s]->uy;
+        ph.open_rho[s] = sides[s]->rho;
+        ph.open_u_f[s][0] = (float)sides[s]->ux;
+        ph.open_u_f[s][1] = (float)sides[s]->uy;
+        ph.open_rho_f[s] = (float)sides[s]->rho;
+    }
     // FP32 constants from the rounded omega in FP32 arithmetic, so that
     // om1_f + omega_f == 1 exactly (1 - omega is exact for omega in (0, 2)):
     // otherwise BGK would scale mass and momentum by (om1 + omega) each step.
@@ -277,6 +311,9 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     st = cuda_check(c, cudaMemsetAsync(c->lat[0], 0, pl.lat_bytes, s), "memset lattice");
     if (!st && p->pattern == LBM_TWO_LATTICE)
         st = cuda_check(c, cudaMemsetAsync(c->lat[1], 0, pl.lat_bytes, s), "memset lattice");
+    if (!st && !open.empty())
+        st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_open, open.data(), open.size() * sizeof(int4),
+                                           cudaMemcpyHostToDevice, s), "copy open-side nodes");
     if (!st && p->layout == LBM_DENSE && pl.mask_bytes)
         st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_mask, c->mask.data(), pl.mask_bytes,
                                            cudaMemcpyHostToDevice, s), "copy mask");
@@ -329,6 +366,15 @@ lbm_status lbm_destroy(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_side_values(lbm_ctx *ctx, int side, const void *d_values) {
+    LBM_CTX_CHECK(ctx);
+    if (side < 0 || side > 3 || ctx->phys.open_kind[side] == LBM_SIDE_WALL)
+        return fail(ctx, LBM_ERR_INVALID, "side is not open");
+    if (d_values && ((uintptr_t)d_values % ctx->csize)) return fail(ctx, LBM_ERR_INVALID, "values not aligned");
+    ctx->phys.open_val[side] = d_values;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_force(lbm_ctx *ctx, const void *d_force) {
     LBM_CTX_CHECK(ctx);
     if (d_force && ((uintptr_t)d_force & 15)) return fail(ctx, LBM_ERR_INVALID, "force not 16-byte aligned");
@@ -353,6 +399,11 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     const Geo &g = ctx->geo;
     for (int k = 0; k < n; ++k) {
         cudaError_t e;
+        if (g.nopen) {
+            e = LBM_DISPATCH(ctx->p.precision, launch_open<P>(g, ctx->phys, current_phase(ctx),
+                                                              current_lattice(ctx), ctx->stream));
+            if (e != cudaSuccess) return cuda_check(ctx, e, "open-side kernel");
+        }
         if (ctx->p.pattern == LBM_TWO_LATTICE) {
             const void *a = ctx->lat[ctx->cur];
             void *b = ctx->lat[1 - ctx->cur];
@@ -469,9 +520,14 @@ lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long l
     for (int k = 0; k < n; ++k) {
         if (!h_states[k] || !h_states[k + 1] || ((uintptr_t)h_states[k] & 15) || ((uintptr_t)h_states[k + 1] & 15))
             return fail(ctx, LBM_ERR_INVALID, "bad state pointer");
-        cudaError_t e = LBM_DISPATCH(ctx->p.precision,
-                                     launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE, h_states[k], h_states[k + 1],
-                                                    (unsigned long long)(t0 + k), ctx->stream));
+        cudaError_t e = cudaSuccess;
+        if (ctx->geo.nopen)
+            e = LBM_DISPATCH(ctx->p.precision, launch_open<P>(ctx->geo, ctx->phys, PH_PLAIN, h_states[k],
+                                                              ctx->stream));
+        if (e == cudaSuccess)
+            e = LBM_DISPATCH(ctx->p.precision,
+                             launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE, h_states[k], h_states[k + 1],
+                                            (unsigned long long)(t0 + k), ctx->stream));
         if (e != cudaSuccess) return cuda_check(ctx, e, "forward_states kernel");
     }
     return LBM_OK;
@@ -482,6 +538,7 @@ lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n, void *
     LBM_CTX_CHECK(ctx);
     if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
         return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
+    if (ctx->phys.has_open) return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint of open sides is not available");
     if (n < 0 || (n > 0 && (!h_states || !d_lambda || !d_lambda_tmp || !d_grad_force)))
         return fail(ctx, LBM_ERR_INVALID, "bad backward arguments");
     if (((uintptr_t)d_lambda & 15) || ((uintptr_t)d_lambda_tmp & 15) || ((uintptr_t)d_grad_force & 15))
@@ -507,6 +564,7 @@ lbm_status lbm_macros_backward(lbm_ctx *ctx, const void *d_grad_rho, const void 
     LBM_CTX_CHECK(ctx);
     if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
         return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
+    if (ctx->phys.has_open) return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint of open sides is not available");
     if (!d_lambda) return fail(ctx, LBM_ERR_INVALID, "d_lambda is NULL");
     return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision,
                                         launch_macros_adjoint<P>(ctx->geo, ctx->phys, ctx->lat[ctx->cur],
@@ -535,8 +593,9 @@ lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id
     if (check_params(p)) return LBM_ERR_INVALID;
     std::vector<uint8_t> mask;
     std::vector<int32_t> tid, nbr, txy;
+    std::vector<int4> open;
     Plan pl;
-    make_plan(*p, mask, tid, nbr, txy, pl);
+    make_plan(*p, mask, tid, nbr, txy, open, pl);
     if (h_mask) std::memcpy(h_mask, mask.data(), mask.size());
     if (p->layout == LBM_SPARSE_TILE16) {
         if (h_tile_id) std::memcpy(h_tile_id, tid.data(), tid.size() * 4);

@@ -72,8 +72,10 @@ template <> struct St<LBM_F32> {
 // finite.  The time step rounds stochastically (enc_sr): the 13 mantissa
 // bits that binary16 drops get 13 uniform random bits added before
 // truncation, so the rounding error has zero mean instead of repeating
-// itself step after step in a slowly varying flow; values below binary16's
-// normal range round to nearest.
+// itself step after step in a slowly varying flow.  Below binary16's normal
+// range (|f_i - w_i| < 2^-24) the same dither is smaller than the subnormal
+// step, so those values round toward zero more often than not (bias below
+// one subnormal step, 2^-34 in f_i - w_i).
 template <> struct St<LBM_F16S> {
     typedef unsigned short R;
     typedef float C;
@@ -81,11 +83,8 @@ template <> struct St<LBM_F16S> {
     static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)) * (1.0f / 1024.0f); }
     static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c * 1024.0f)); }
     static __device__ __forceinline__ R enc_sr(C c, unsigned rnd) {
-        const float v = c * 1024.0f;
-        const unsigned b = __float_as_uint(v);
-        const bool normal = (b & 0x7F800000u) >= (113u << 23); // |v| >= 2^-14
-        const __half h = normal ? __float2half_rz(__uint_as_float(b + (rnd >> 19))) : __float2half_rn(v);
-        return __half_as_ushort(h);
+        const unsigned b = __float_as_uint(c * 1024.0f) + (rnd >> 19);
+        return __half_as_ushort(__float2half_rz(__uint_as_float(b)));
     }
 };
 
@@ -785,14 +784,14 @@ template <int P, bool HAS_MASK> struct MinBlocks {
 
 template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
 __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
-    k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0, unsigned step) {
+    k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0, int ystride, unsigned step) {
     typedef StV<P, A::VEC_> S;
     typedef typename S::R R;
     typedef typename S::C C;
     constexpr int VEC = S::VEC;
     const R *src = reinterpret_cast<const R *>(src_v);
     R *dst = reinterpret_cast<R *>(dst_v);
-    A ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + (int)blockIdx.y);
+    A ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + ystride * (int)blockIdx.y);
     const int lane = threadIdx.x & 31;
 
     unsigned long long mv = 0;
@@ -1001,6 +1000,76 @@ __device__ __forceinline__ void gather_node(const Geo &g, const Phys &ph, int ph
     }
 }
 
+// Open side `side` at boundary node (x, y) (Zou & He, for any side): the
+// links of mask m that pull from beyond the side are unknown; the known
+// shifted values f' fix rho (1 + u.n) = 1 + sum_{c.n=0} f'_j + 2 sum_{c.n>0} f'_j
+// (the weights of those links sum to 1), with u given (velocity side) or rho
+// given and u = (u.n) n (pressure side); then
+//   f'_i = f'_opp(i) + 6 w_i rho (c_i . u) - (c_i . t) N_t,
+//   N_t = 1/2 sum_{c.n=0} (c_j . t) f'_j - rho (u . t)/3.
+// Returns the set of links it wrote (bit i).
+template <class C>
+__device__ unsigned open_side(const Geo &g, const Phys &ph, int x, int y, int side, unsigned m, C f[9]) {
+    unsigned unk = 0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        if (((m >> (i - 1)) & 1u) && wall_side(g, x, y, i) == side) unk |= 1u << i;
+    if (!unk) return 0u;
+    const int nx_ = side == 0 ? -1 : (side == 1 ? 1 : 0), ny_ = side == 2 ? -1 : (side == 3 ? 1 : 0);
+    const int tx = nx_ == 0, ty = ny_ == 0;
+    C d = C(0), st = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cn = cx(i) * nx_ + cy(i) * ny_;
+        if (cn == 0) {
+            d += f[i];
+            st += C(cx(i) * tx + cy(i) * ty) * f[i];
+        } else if (cn > 0) {
+            d += C(2) * f[i];
+        }
+    }
+    const int k = side < 2 ? y : x, len = side < 2 ? g.ny : g.nx;
+    const C *val = reinterpret_cast<const C *>(ph.open_val[side]);
+    C rho, ux, uy;
+    if (ph.open_kind[side] == LBM_SIDE_VELOCITY) {
+        if (val) {
+            ux = val[k];
+            uy = val[len + k];
+        } else if constexpr (sizeof(C) == 8) {
+            ux = ph.open_u[side][0];
+            uy = ph.open_u[side][1];
+        } else {
+            ux = ph.open_u_f[side][0];
+            uy = ph.open_u_f[side][1];
+        }
+        rho = (C(1) + d) / (C(1) + (C(nx_) * ux + C(ny_) * uy));
+    } else {
+        if (val) rho = val[k];
+        else if constexpr (sizeof(C) == 8) rho = ph.open_rho[side];
+        else rho = ph.open_rho_f[side];
+        const C un = (C(1) + d - rho) / rho;
+        ux = C(nx_) * un;
+        uy = C(ny_) * un;
+    }
+    const C Nt = C(0.5) * st - rho * (C(tx) * ux + C(ty) * uy) * C(1.0 / 3.0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        if ((unk >> i) & 1u)
+            f[i] = f[opp(i)] + C(6) * wgt<C>(i) * rho * (C(cx(i)) * ux + C(cy(i)) * uy) -
+                   C(cx(i) * tx + cy(i) * ty) * Nt;
+    return unk;
+}
+
+// Every open side whose row or column holds (x, y).
+template <class C>
+__device__ __forceinline__ void apply_open(const Geo &g, const Phys &ph, int x, int y, unsigned m, C f[9]) {
+    if (!ph.has_open || m == 0u) return;
+    const bool on[4] = {x == 0, x == g.nx - 1, y == 0, y == g.ny - 1};
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (ph.open_kind[s] != LBM_SIDE_WALL && on[s]) open_side<C>(g, ph, x, y, s, m, f);
+}
+
 template <class C>
 __device__ __forceinline__ void node_force(const Geo &g, const Phys &ph, long long n, C &Fx, C &Fy) {
     if (ph.force_mode == FORCE_FIELD) {
@@ -1013,10 +1082,13 @@ __device__ __forceinline__ void node_force(const Geo &g, const Phys &ph, long lo
     }
 }
 
+// One thread per node on a 2-D grid: x along blockIdx.x, rows on blockIdx.y
+// (blockIdx.z counts chunks of gridDim.y rows).  No integer division.
 #define LBM_NODE_LOOP(g)                                                                   \
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;                  \
-    if (n >= (long long)(g).nx * (g).ny) return;                                           \
-    const int y = (int)(n / (g).nx), x = (int)(n - (long long)y * (g).nx);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);                            \
+    const int y = (int)(blockIdx.z * gridDim.y + blockIdx.y);                              \
+    if (x >= (g).nx || y >= (g).ny) return;                                                \
+    const long long n = (long long)y * (g).nx + x;
 
 template <int P>
 __global__ void k_init(const Geo g, int phase, const void *rho_v, const void *u_v, void *lat_v) {
@@ -1091,6 +1163,7 @@ __global__ void k_macros(const Geo g, const Phys ph, int phase, const void *lat_
     if (m != 0xFFu) {
         C f[9];
         gather_node<S>(g, ph, phase, reinterpret_cast<const typename S::R *>(lat_v), x, y, m, f);
+        apply_open<C>(g, ph, x, y, m, f);
         C Fx, Fy, drho, inv;
         node_force<C>(g, ph, n, Fx, Fy);
         moments<C, true>(f, Fx, Fy, drho, r, inv, ux, uy);
@@ -1131,23 +1204,25 @@ __global__ void __launch_bounds__(AUX_BLOCK) k_reduce(const Geo g, const Phys ph
     const typename S::R *M = reinterpret_cast<const typename S::R *>(lat_v);
     const C *tgt = reinterpret_cast<const C *>(target_v);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const long long N = (long long)g.nx * g.ny;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(n / g.nx), x = (int)(n - (long long)y * g.nx);
+    for (int y = blockIdx.x; y < g.ny; y += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+        const long long n = (long long)y * g.nx + x;
         const unsigned m = node_mask(g, x, y);
         if (m == 0xFFu) continue;
         if (kind == 0) {
+            // the node's own 9 values summed in the storage's compute type
+            // (error ~1e-7 of the node's deviation from w), accumulated over
+            // nodes in FP64
+            C v[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const double v = (double)canon_read<S>(g, phase, M, x, y, i, m);
-                acc[0] += v;
-                acc[1] += cx(i) * v;
-                acc[2] += cy(i) * v;
-            }
+            for (int i = 0; i < 9; ++i) v[i] = canon_read<S>(g, phase, M, x, y, i, m);
+            acc[0] += (double)((((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8]);
+            acc[1] += (double)(((v[1] - v[3]) + (v[5] - v[7])) + (v[8] - v[6]));
+            acc[2] += (double)(((v[2] - v[4]) + (v[5] - v[7])) + (v[6] - v[8]));
         } else {
             C f[9];
             gather_node<S>(g, ph, phase, M, x, y, m, f);
+            apply_open<C>(g, ph, x, y, m, f);
             C Fx, Fy, drho, r, inv, ux, uy;
             node_force<C>(g, ph, n, Fx, Fy);
             moments<C, true>(f, Fx, Fy, drho, r, inv, ux, uy);
@@ -1169,6 +1244,28 @@ __global__ void __launch_bounds__(AUX_BLOCK) k_reduce_final(const double *partia
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] += partial[4 * p + c];
     block_sum4(acc, out);
+}
+
+// Open sides, before a step: each boundary node's links that pull from beyond
+// its open side get their open-side values, stored where the step reads a
+// bounced link (own slot opp(i) in the plain phase, own slot i in the AA
+// phases).  Only the node's own bounce reads those slots, and the step
+// overwrites them, so the state between steps stays canonical.
+template <int P>
+__global__ void k_open(const Geo g, const Phys ph, int phase, void *lat_v) {
+    typedef St<P> S;
+    typedef typename S::C C;
+    const int e = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= g.nopen) return;
+    const int4 b = g.open_nodes[e];
+    const unsigned m = node_mask(g, b.x, b.y);
+    typename S::R *M = reinterpret_cast<typename S::R *>(lat_v);
+    C f[9];
+    gather_node<S>(g, ph, phase, M, b.x, b.y, m, f);
+    const unsigned unk = open_side<C>(g, ph, b.x, b.y, b.z, m, f);
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        if ((unk >> i) & 1u) M[cidx(g, b.x, b.y, phase == PH_PLAIN ? opp(i) : i)] = S::enc(f[i]);
 }
 
 // Transpose of the macros at the current (two-lattice, dense) state.
@@ -1238,48 +1335,76 @@ template <int VEC> static Shape step_shape(const Geo &g) {
     return sh;
 }
 
+// Rows row0, row0 + stride, ... (nrows of them) of the dense layout; all
+// kept tiles of the tiled layout.
+struct Rows {
+    int row0, nrows, stride;
+};
 template <int P, class A, int MODE, bool HM, int F>
-static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, cudaStream_t s) {
+static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
+                               cudaStream_t s) {
     const Shape sh = step_shape<A::VEC_>(g);
     if (sh.gx == 0) return cudaSuccess;
-    for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
-        const unsigned gy = sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u;
-        k_step<P, A, MODE, HM, F><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, (int)y0, t);
+    const unsigned rows = sh.dense ? (unsigned)r.nrows : 1u;
+    for (unsigned k = 0; k < rows; k += 65535u) {
+        const unsigned gy = rows - k < 65535u ? rows - k : 65535u;
+        k_step<P, A, MODE, HM, F><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, r.row0 + (int)k * r.stride,
+                                                                    r.stride, t);
     }
     return cudaGetLastError();
 }
 template <int P, class A, int MODE, bool HM>
-static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, cudaStream_t s) {
+static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
+                              cudaStream_t s) {
     switch (ph.force_mode) {
-    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, src, dst, t, s);
-    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, t, s);
-    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, src, dst, t, s);
+    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, src, dst, t, r, s);
+    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, t, r, s);
+    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, src, dst, t, r, s);
     }
 }
 template <int P, class A, bool HM>
-static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned t,
+static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned t, Rows r,
                              cudaStream_t s) {
     switch (mode) {
-    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, src, dst, t, s);
-    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, t, s);
-    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, src, dst, t, s);
+    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, src, dst, t, r, s);
+    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, t, r, s);
+    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, src, dst, t, r, s);
     }
 }
 
+// Dense grids whose only bounced links are in the first and last row (walls
+// or open sides in y, periodic x, no obstacle): those two rows run the
+// masked kernel, every other row the kernel without a mask.  Both read the
+// state before the step and write disjoint nodes (two-lattice), or touch
+// disjoint slot sets (AA), so the split is exact.
 template <int P>
 cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned long long t,
                         cudaStream_t s) {
     constexpr int VM = StepVec<P, true>::value, VN = StepVec<P, false>::value;
     const unsigned tt = (unsigned)t;
+    const Rows all = {0, g.ny, 1};
     if (g.layout == LBM_DENSE) {
-        if (g.has_mask) return step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, tt, s);
-        return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, tt, s);
+        if (g.has_mask && g.frame_y) {
+            cudaError_t e = step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, tt, Rows{0, 2, g.ny - 1}, s);
+            if (e != cudaSuccess) return e;
+            return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, tt, Rows{1, g.ny - 2, 1}, s);
+        }
+        if (g.has_mask) return step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, tt, all, s);
+        return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, tt, all, s);
     }
-    return step_mode<P, TileAddr<VM>, true>(g, ph, mode, src, dst, tt, s);
+    return step_mode<P, TileAddr<VM>, true>(g, ph, mode, src, dst, tt, all, s);
 }
 
-static inline unsigned node_blocks(const Geo &g) {
-    return (unsigned)(((long long)g.nx * g.ny + AUX_BLOCK - 1) / AUX_BLOCK);
+static inline dim3 node_blocks(const Geo &g) {
+    const unsigned rows = (unsigned)(g.ny < 65535 ? g.ny : 65535);
+    return dim3((unsigned)((g.nx + AUX_BLOCK - 1) / AUX_BLOCK), rows, (unsigned)((g.ny + rows - 1) / rows));
+}
+
+template <int P>
+cudaError_t launch_open(const Geo &g, const Phys &ph, int phase, void *lat, cudaStream_t s) {
+    if (g.nopen == 0) return cudaSuccess;
+    k_open<P><<<(g.nopen + 127) / 128, 128, 0, s>>>(g, ph, phase, lat);
+    return cudaGetLastError();
 }
 
 template <int P>
@@ -1350,6 +1475,7 @@ cudaError_t launch_macros_adjoint(const Geo &g, const Phys &ph, const void *stat
     template cudaError_t launch_adjoint<P>(const Geo &, const Phys &, const void *, const void *, void *,  \
                                            void *, cudaStream_t);                                           \
     template cudaError_t launch_macros_adjoint<P>(const Geo &, const Phys &, const void *, const void *,   \
-                                                  const void *, void *, void *, cudaStream_t);
+                                                  const void *, void *, void *, cudaStream_t);              \
+    template cudaError_t launch_open<P>(const Geo &, const Phys &, int, void *, cudaStream_t);
 
 } // namespace lbm

@@ -42,7 +42,12 @@ class LBMError(RuntimeError):
 
 
 class lbm_side(ctypes.Structure):
-    _fields_ = [("periodic", ctypes.c_int), ("ux", ctypes.c_double), ("uy", ctypes.c_double)]
+    _fields_ = [("periodic", ctypes.c_int), ("ux", ctypes.c_double), ("uy", ctypes.c_double),
+                ("kind", ctypes.c_int), ("rho", ctypes.c_double)]
+
+
+LBM_SIDE_WALL, LBM_SIDE_VELOCITY, LBM_SIDE_PRESSURE = 0, 1, 2
+SIDES = ("west", "east", "south", "north")
 
 
 class lbm_params(ctypes.Structure):
@@ -75,6 +80,7 @@ def _load():
         "lbm_create": ([_P, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)], st),
         "lbm_destroy": ([_vp], st),
         "lbm_set_force": ([_vp, _vp], st),
+        "lbm_set_side_values": ([_vp, ctypes.c_int, _vp], st),
         "lbm_init_equilibrium": ([_vp, _vp, _vp], st),
         "lbm_step": ([_vp, ctypes.c_int], st),
         "lbm_macros": ([_vp, _vp, _vp], st),
@@ -153,6 +159,10 @@ def lbm_create(p: lbm_params, workspace: torch.Tensor):
 
 def lbm_destroy(ctx):
     _check("lbm_destroy", _load().lbm_destroy(ctx))
+
+
+def lbm_set_side_values(ctx, side: int, values: Optional[torch.Tensor]):
+    _check("lbm_set_side_values", _load().lbm_set_side_values(ctx, int(side), _ptr(values)), ctx)
 
 
 def lbm_set_force(ctx, force: Optional[torch.Tensor]):
@@ -304,9 +314,10 @@ def lbm_last_error(ctx) -> str:
 def make_params(nx: int, ny: int, tau: float, solid: Optional[np.ndarray] = None,
                 force=(0.0, 0.0), periodic_x: bool = True, periodic_y: bool = True,
                 walls=None, precision="f32", layout="dense", pattern="two_lattice",
-                stream=None):
+                stream=None, open=None):
     """lbm_params from Python values.  walls: {"west"|"east"|"south"|"north":
-    (ux, uy)} velocities of wall sides (axes not periodic).  Returns
+    (ux, uy)} velocities of wall sides (axes not periodic).  open: {side name:
+    ("velocity", (ux, uy)) | ("pressure", rho)} open sides.  Returns
     (params, keepalive) -- keepalive holds the solid array while params is used."""
     p = lbm_params()
     p.nx, p.ny = int(nx), int(ny)
@@ -322,6 +333,16 @@ def make_params(nx: int, ny: int, tau: float, solid: Optional[np.ndarray] = None
         s = getattr(p, name)
         s.periodic = int(bool(per))
         s.ux, s.uy = walls.get(name, (0.0, 0.0))
+    for name, (kind, val) in (open or {}).items():
+        s = getattr(p, name)
+        if kind == "velocity":
+            s.kind = LBM_SIDE_VELOCITY
+            s.ux, s.uy = float(val[0]), float(val[1])
+        elif kind == "pressure":
+            s.kind = LBM_SIDE_PRESSURE
+            s.rho = float(val)
+        else:
+            raise ValueError("open side kind must be 'velocity' or 'pressure'")
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
     p.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
@@ -336,10 +357,10 @@ class LBM:
 
     def __init__(self, nx: int, ny: int, tau: float, solid=None, force=(0.0, 0.0),
                  periodic_x: bool = True, periodic_y: bool = True, walls=None,
-                 precision="f32", layout="dense", pattern="two_lattice", device="cuda"):
+                 precision="f32", layout="dense", pattern="two_lattice", device="cuda", open=None):
         self.nx, self.ny = int(nx), int(ny)
         self.params, keep = make_params(nx, ny, tau, solid, force, periodic_x, periodic_y, walls,
-                                        precision, layout, pattern)
+                                        precision, layout, pattern, open=open)
         self.precision = self.params.precision
         self.dtype = torch.float64 if self.precision == LBM_F64 else torch.float32
         self.device = torch.device(device)
@@ -349,6 +370,7 @@ class LBM:
         del keep
         self.params.solid = None
         self._force = None
+        self._side_vals = [None] * 4
 
     # resources -------------------------------------------------------------
     def close(self):
@@ -375,6 +397,19 @@ class LBM:
         t = torch.as_tensor(a, dtype=self.dtype, device=self.device).contiguous()
         assert tuple(t.shape) == tuple(shape), (t.shape, shape)
         return t
+
+    def set_side_values(self, side, values=None):
+        """Per-node values of an open side (velocity [2, len], pressure
+        [len]); None returns to the uniform value."""
+        k = SIDES.index(side) if isinstance(side, str) else int(side)
+        if values is None:
+            self._side_vals[k] = None
+        else:
+            length = self.ny if k < 2 else self.nx
+            kind = getattr(self.params, SIDES[k]).kind
+            shape = (2, length) if kind == LBM_SIDE_VELOCITY else (length,)
+            self._side_vals[k] = self._t(values, shape)
+        lbm_set_side_values(self.ctx, k, self._side_vals[k])
 
     def set_force(self, force=None):
         self._force = None if force is None else self._t(force, (2, self.ny, self.nx))

@@ -28,16 +28,26 @@ class Case:
     rho0: np.ndarray = None
     u0: np.ndarray = None
     force_field: np.ndarray = None
+    # open sides {side name: ("velocity", (ux, uy)) | ("pressure", rho)}, and
+    # optional per-node values along a side {side name: array}
+    open: dict = field(default_factory=dict)
+    open_vals: dict = field(default_factory=dict)
 
 
 def oracle_setup(orc, c: Case):
+    op = {}
+    for name, (kind, val) in c.open.items():
+        op[SIDES.index(name)] = (kind, c.open_vals.get(name, val))
     return orc.Setup(nx=c.nx, ny=c.ny, tau=c.tau, periodic_x=c.px, periodic_y=c.py,
-                     wall_u=[tuple(c.walls.get(s, (0.0, 0.0))) for s in SIDES], force=c.force)
+                     wall_u=[tuple(c.walls.get(s, (0.0, 0.0))) for s in SIDES], force=c.force, open=op)
 
 
 def gpu_kwargs(c: Case):
-    return dict(nx=c.nx, ny=c.ny, tau=c.tau, solid=c.solid, force=c.force, periodic_x=c.px,
-                periodic_y=c.py, walls=c.walls)
+    kw = dict(nx=c.nx, ny=c.ny, tau=c.tau, solid=c.solid, force=c.force, periodic_x=c.px,
+              periodic_y=c.py, walls=c.walls)
+    if c.open:
+        kw["open"] = c.open
+    return kw
 
 
 def cavity(n=128, tau=0.6, lid=0.1):

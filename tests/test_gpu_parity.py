@@ -239,3 +239,32 @@ def test_step_count_and_zero_steps(L):
     assert torch.equal(sim.get_f(), f0) and sim.steps == 0
     sim.step(3)
     assert sim.steps == 3
+
+
+@pytest.mark.parametrize("layout,pattern", VARIANTS)
+@pytest.mark.parametrize("steps", [1, 2, 41])
+def test_wall_rows_split_fp64_matches_oracle(L, orc, layout, pattern, steps):
+    """Periodic x, moving walls in y, no obstacle: the dense layout runs the
+    wall rows with the masked kernel and the other rows without a mask."""
+    nx, ny = 64, 24
+    case = C.Case("wallrows%dx%d" % (nx, ny), nx, ny, 0.7, px=True, py=False,
+                  walls={"south": (0.03, 0.0), "north": (-0.02, 0.0)}, force=(1e-5, -2e-6))
+    case.rho0 = 1.0 + 0.01 * inputs.random_field((ny, nx), 711)
+    case.u0 = 0.03 * inputs.random_field((2, ny, nx), 712)
+    o = oracle_cached(orc, case, steps)
+    g = run_gpu(L, case, steps, "f64", layout, pattern)
+    assert C.rel_l2(g["f"], o["f"]) <= 1e-12
+    assert C.rel_l2(g["u"], o["u"]) <= 1e-11
+
+
+@pytest.mark.parametrize("precision,tol", [("f32", 1e-5), ("f16s", 5e-3)])
+def test_wall_rows_split_low_precision(L, orc, precision, tol):
+    nx, ny = 128, 64
+    fx, rho, u = inputs.poiseuille(nx, ny, 0.8, 0.05)
+    case = C.Case("pois%dx%d" % (nx, ny), nx, ny, 0.8, px=True, py=False, force=(fx, 0.0))
+    case.rho0, case.u0 = rho, u + 0.01 * inputs.random_field((2, ny, nx), 713)
+    o = oracle_cached(orc, case, 300)
+    for layout, pattern in VARIANTS:
+        g = run_gpu(L, case, 300, precision, layout, pattern)
+        err = C.rel_l2(g["u"], o["u"])
+        assert err <= tol, (layout, pattern, err)

@@ -95,3 +95,41 @@ def test_sides_order_matches_header(lbm):
                            walls={"west": (1, 2), "east": (3, 4), "south": (5, 6), "north": (7, 8)}, stream=0)
     got = [(getattr(p, s).ux, getattr(p, s).uy) for s in SIDES]
     assert got == [(1, 2), (3, 4), (5, 6), (7, 8)]
+
+
+@pytest.mark.parametrize("bad", ["adjacent", "periodic", "rho", "speed"])
+def test_invalid_open_sides_rejected(lbm, bad):
+    kw = dict(periodic_x=False, periodic_y=False)
+    if bad == "adjacent":
+        kw["open"] = {"west": ("velocity", (0.05, 0.0)), "north": ("pressure", 1.0)}
+    elif bad == "periodic":
+        kw = dict(periodic_x=True, periodic_y=False, open={"west": ("velocity", (0.05, 0.0))})
+    elif bad == "rho":
+        kw["open"] = {"east": ("pressure", 0.0)}
+    else:
+        kw["open"] = {"west": ("velocity", (-1.5, 0.0))}
+    p, _ = lbm.make_params(32, 16, 0.8, stream=0, **kw)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_workspace_bytes(p)
+    assert e.value.status == lbm.LBM_ERR_INVALID
+
+
+@pytest.mark.parametrize("sides", [("west", "east"), ("south", "north"), ("east", None)])
+def test_geometry_with_open_sides_matches_oracle(lbm, orc, sides):
+    """Links across an open side are marked like links across a wall; the
+    mask and the tile tables match the oracle's."""
+    nx, ny = 48, 32
+    solid = inputs.random_solid(nx, ny, 0.2, seed=77)
+    along_x = sides[0] in ("west", "east")
+    op = {sides[0]: ("velocity", (0.02, 0.01))}
+    if sides[1]:
+        op[sides[1]] = ("pressure", 1.0)
+    s = orc.Setup(nx=nx, ny=ny, tau=0.8, periodic_x=not along_x, periodic_y=along_x,
+                  open={SIDES.index(k): v for k, v in op.items()})
+    omask, onf = orc.link_mask(s, solid)
+    otid, onbr = orc.tile_map(s, omask)
+    p, keep = lbm.make_params(nx, ny, 0.8, solid=solid, periodic_x=not along_x, periodic_y=along_x,
+                              layout="sparse", stream=0, open=op)
+    mask, tid, nbr, nf = lbm.lbm_geometry(p)
+    assert np.array_equal(mask, omask) and nf == onf
+    assert np.array_equal(tid, otid) and np.array_equal(nbr, onbr)
