@@ -368,10 +368,19 @@ def run_reference_arm(args):
 
 
 def cpu_baseline_leg(n: int):
+    """The oracle on all host threads (the reported value) and on one thread."""
+    from oracle import oracle as orc
+    orc.build()
+    threads = orc.num_threads()
+    orc.set_threads(1)
+    g1, steps1, dt1, _ = oracle_glups(n, 4.0)
+    orc.set_threads(threads)
     g, steps, dt, cores = oracle_glups(n, 12.0)
     return {"value": round(g, 5), "unit": "GLUPS", "cores": cores, "kind": "oracle",
+            "single_thread_value": round(g1, 5),
             "sample": "FP64 oracle, %d x %d periodic Taylor-Green, %d steps in %.1f s on %d host threads "
-                      "(%d cores in the affinity mask)" % (n, n, steps, dt, cores, cpu_cores())}
+                      "(%d cores in the affinity mask); one thread: %d steps in %.1f s"
+                      % (n, n, steps, dt, cores, cpu_cores(), steps1, dt1)}
 
 
 # ---------------------------------------------------------------- extra lines

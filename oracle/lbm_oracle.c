@@ -52,6 +52,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the later parallel loops (timing of the oracle only). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 void orc_lattice(int cx[9], int cy[9], double w[9], int opp[9])
 {
     for (int i = 0; i < 9; ++i) {

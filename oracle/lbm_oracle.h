@@ -78,5 +78,6 @@ void orc_macros_adjoint(const orc_params *p, const uint8_t *mask,
 void orc_step_cs(const orc_params *p, const uint8_t *mask, const double *force,
                  const double *A, double *B);
 int  orc_num_threads(void);
+void orc_set_threads(int n);
 
 #endif

@@ -136,6 +136,7 @@ def lib():
         L.orc_adjoint_step.argtypes = [P, dp, dp, dp, dp, dp, dp]
         L.orc_macros_adjoint.argtypes = [P, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -155,6 +156,11 @@ def _f64(a, shape=None):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel step loop (for timing it)."""
+    lib().orc_set_threads(int(n))
 
 
 def lattice():

@@ -20,6 +20,7 @@
 //  * every variant (dense / tiled, two-lattice / AA) feeds the same
 //    `collide` with the same operands, so FP64 variants agree bit for bit.
 #pragma once
+#include <type_traits>
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -49,20 +50,24 @@ template <class C> __host__ __device__ constexpr C wgt(int i) {
 
 template <int P> struct St;
 // dec/enc convert between the stored element and f_i - w_i in the compute
-// type; enc_sr is the encode of the time step, given 32 random bits.
+// type.  The step kernel works in units of SCALE (f_i - w_i times SCALE):
+// dec_step decodes into them, enc_sr (given 32 random bits) encodes from
+// them; every other kernel uses dec/enc.
 template <> struct St<LBM_F64> {
     typedef double R; // stored element
     typedef double C; // compute type
-    enum { VEC = 2, STOCHASTIC = 0 };
+    enum { VEC = 2, STOCHASTIC = 0, SCALE = 1 };
     static __device__ __forceinline__ C dec(R r) { return r; }
+    static __device__ __forceinline__ C dec_step(R r) { return r; }
     static __device__ __forceinline__ R enc(C c) { return c; }
     static __device__ __forceinline__ R enc_sr(C c, unsigned) { return c; }
 };
 template <> struct St<LBM_F32> {
     typedef float R;
     typedef float C;
-    enum { VEC = 4, STOCHASTIC = 0 };
+    enum { VEC = 4, STOCHASTIC = 0, SCALE = 1 };
     static __device__ __forceinline__ C dec(R r) { return r; }
+    static __device__ __forceinline__ C dec_step(R r) { return r; }
     static __device__ __forceinline__ R enc(C c) { return c; }
     static __device__ __forceinline__ R enc_sr(C c, unsigned) { return c; }
 };
@@ -79,11 +84,12 @@ template <> struct St<LBM_F32> {
 template <> struct St<LBM_F16S> {
     typedef unsigned short R;
     typedef float C;
-    enum { VEC = 4, STOCHASTIC = 1 }; // 8-byte vectors: 4 nodes per thread
+    enum { VEC = 4, STOCHASTIC = 1, SCALE = 1024 }; // 8-byte vectors: 4 nodes per thread
     static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)) * (1.0f / 1024.0f); }
     static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c * 1024.0f)); }
+    static __device__ __forceinline__ C dec_step(R r) { return __half2float(__ushort_as_half(r)); }
     static __device__ __forceinline__ R enc_sr(C c, unsigned rnd) {
-        const unsigned b = __float_as_uint(c * 1024.0f) + (rnd >> 19);
+        const unsigned b = __float_as_uint(c) + (rnd >> 19);
         return __half_as_ushort(__float2half_rz(__uint_as_float(b)));
     }
 };
@@ -112,11 +118,22 @@ template <> struct VecWord<8> { typedef uint2 T; static __device__ __forceinline
 template <int P, int V> struct StV : St<P> {
     enum { VEC = V };
 };
-// Nodes per thread of the step kernel: FP32 with a link mask moves 2 nodes
-// (8-byte vectors) so the bounce-back state fits 4 blocks per SM; otherwise
-// one 16-byte (FP64, FP32) or 8-byte (FP16s) vector.
-template <int P, bool HAS_MASK> struct StepVec {
-    enum { value = (P == LBM_F32 && HAS_MASK) ? 2 : St<P>::VEC };
+// Nodes per thread of the step kernel: one 16-byte (FP64, FP32) or 8-byte
+// (FP16s) vector.  FP32 with a link mask moves 2 nodes (8-byte vectors), so
+// that the preloaded bounce-back state fits 4 blocks per SM, in the AA steps,
+// with a per-node force field and in the adjoint; its two-lattice step
+// without a force field moves 4 (bounced values loaded on demand).
+template <int P, bool HAS_MASK, int MODE = MODE_AA_PULLPUSH, int FORCE = FORCE_NONE> struct StepVec {
+    enum {
+        value = (P == LBM_F32 && HAS_MASK && (MODE != MODE_TWO_LATTICE || FORCE == FORCE_FIELD)) ? 2 : St<P>::VEC
+    };
+};
+// Whether the step preloads the own-node vectors its bounced links read
+// (issued with the gather, one vector per needed slot) or loads each bounced
+// value when the node needs it: the FP32 two-lattice step with 16-byte
+// vectors loads on demand, which keeps it at 4 blocks per SM.
+template <class S, int MODE> struct OwnPreload {
+    enum { value = !(sizeof(typename S::R) == 4 && S::VEC == 4 && MODE == MODE_TWO_LATTICE) };
 };
 
 template <class R, int VEC> union V16 {
@@ -355,22 +372,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // momentum j = m + F/2 = rho u.  COMP: j is returned as jx + jxl exactly
 // (TwoSum), because F/2 is often below half an ulp of m and rounding it away
 // would bias the momentum gain the same way every step.
-template <class C, bool HAS_F, bool COMP = false>
+// SC: f' in units of SC (f - w times SC); drho, jx, jy come out in those
+// units, rho, inv and u in plain ones (inv = 1 / (SC rho), so u = j inv).
+template <class C, bool HAS_F, bool COMP = false, int SC = 1>
 __device__ __forceinline__ void moments_j(const C f[9], C Fx, C Fy, C &drho, C &rho, C &inv, C &ux, C &uy,
                                           C &jx, C &jy, C &jxl, C &jyl) {
     drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    rho = C(1) + drho;
+    rho = C(1) + drho * C(1.0 / SC);
     const C mx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
     const C my = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
-    inv = recip(rho);
+    inv = recip(rho) * C(1.0 / SC);
     jxl = jyl = C(0);
     if (HAS_F) {
         if constexpr (COMP) {
             two_sum(mx, C(0.5) * Fx, jx, jxl);
             two_sum(my, C(0.5) * Fy, jy, jyl);
         } else {
-            jx = mx + C(0.5) * Fx;
-            jy = my + C(0.5) * Fy;
+            jx = mx + C(0.5 * SC) * Fx;
+            jy = my + C(0.5 * SC) * Fy;
         }
     } else {
         jx = mx;
@@ -416,21 +435,27 @@ template <class C> struct Coef {
 // bias that grows linearly with the step count in slowly varying flows.
 // FP16s storage rounding (2^-21 relative to w_i) dwarfs that bias, so its
 // kernels keep the cheaper form 3 omega w_i rho (c_i . u).
-template <class C, bool HAS_F, bool COMP>
+// SC: f in units of SC (the FP16s step works in f - w times 2^10, so its
+// decode and encode need no scaling); the constants that multiply plain
+// quantities (rho, u, F) carry the factor.
+template <class C, bool HAS_F, bool COMP, int SC = 1>
 __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
+    static_assert(SC == 1 || !COMP, "the compensated form works in plain units");
     C drho, rho, inv, ux, uy, jx, jy, jxl, jyl;
-    moments_j<C, HAS_F, COMP>(f, Fx, Fy, drho, rho, inv, ux, uy, jx, jy, jxl, jyl);
+    moments_j<C, HAS_F, COMP, SC>(f, Fx, Fy, drho, rho, inv, ux, uy, jx, jy, jxl, jyl);
     const C usq = C(1.5) * (ux * ux + uy * uy);
     const C om = co.om, om1 = co.om1;
-    // omega * w_q * rho and omega * w_q * drho per weight class
-    const C R0 = (om * C(4.0 / 9.0)) * rho, Ra = (om * C(1.0 / 9.0)) * rho, Rd = (om * C(1.0 / 36.0)) * rho;
+    // omega * w_q * rho (times SC) and omega * w_q * drho per weight class
+    const C rs = rho * C(SC);
+    const C R0 = (om * C(4.0 / 9.0)) * rs, Ra = (om * C(1.0 / 9.0)) * rs, Rd = (om * C(1.0 / 36.0)) * rs;
     const C E0 = (om * C(4.0 / 9.0)) * drho, Ea = (om * C(1.0 / 9.0)) * drho, Ed = (om * C(1.0 / 36.0)) * drho;
     C uF = C(0), K0 = C(0), Ka = C(0), Kd = C(0);
     if (HAS_F) {
         uF = ux * Fx + uy * Fy;
-        K0 = co.kk * C(4.0 / 9.0);
-        Ka = co.kk * C(1.0 / 9.0);
-        Kd = co.kk * C(1.0 / 36.0);
+        const C ks = co.kk * C(SC);
+        K0 = ks * C(4.0 / 9.0);
+        Ka = ks * C(1.0 / 9.0);
+        Kd = ks * C(1.0 / 36.0);
     }
     // rest
     {
@@ -591,15 +616,15 @@ __device__ __forceinline__ typename S::R pulled(const V16<typename S::R, S::VEC>
 template <class S, int K, int MODE>
 __device__ __forceinline__ void node_values(const V16<typename S::R, S::VEC> raw[9],
                                             const typename S::R edge[9], typename S::C f[9]) {
-    f[0] = S::dec(pulled<S, 0, K>(raw, edge, MODE));
-    f[1] = S::dec(pulled<S, 1, K>(raw, edge, MODE));
-    f[2] = S::dec(pulled<S, 2, K>(raw, edge, MODE));
-    f[3] = S::dec(pulled<S, 3, K>(raw, edge, MODE));
-    f[4] = S::dec(pulled<S, 4, K>(raw, edge, MODE));
-    f[5] = S::dec(pulled<S, 5, K>(raw, edge, MODE));
-    f[6] = S::dec(pulled<S, 6, K>(raw, edge, MODE));
-    f[7] = S::dec(pulled<S, 7, K>(raw, edge, MODE));
-    f[8] = S::dec(pulled<S, 8, K>(raw, edge, MODE));
+    f[0] = S::dec_step(pulled<S, 0, K>(raw, edge, MODE));
+    f[1] = S::dec_step(pulled<S, 1, K>(raw, edge, MODE));
+    f[2] = S::dec_step(pulled<S, 2, K>(raw, edge, MODE));
+    f[3] = S::dec_step(pulled<S, 3, K>(raw, edge, MODE));
+    f[4] = S::dec_step(pulled<S, 4, K>(raw, edge, MODE));
+    f[5] = S::dec_step(pulled<S, 5, K>(raw, edge, MODE));
+    f[6] = S::dec_step(pulled<S, 6, K>(raw, edge, MODE));
+    f[7] = S::dec_step(pulled<S, 7, K>(raw, edge, MODE));
+    f[8] = S::dec_step(pulled<S, 8, K>(raw, edge, MODE));
 }
 
 // Stored value of slot s at the thread's own node k.  Slots 0, 1, 3 are in
@@ -644,7 +669,7 @@ __device__ __forceinline__ void preload_own(const A &ad, const typename S::R *sr
 // Half-way bounce-back for the links of node k whose mask bit is set:
 // f'_i = (stored post-collision value of link opp(i) at x) + wall term.
 template <class S, int MODE, class A>
-__device__ __forceinline__ void bounce(const Geo &g, const Phys &ph, const A &ad,
+__device__ __forceinline__ void bounce(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                        const V16<typename S::R, S::VEC> raw[9],
                                        const V16<typename S::R, S::VEC> own[9], int k, unsigned m,
                                        typename S::C f[9]) {
@@ -653,9 +678,14 @@ __device__ __forceinline__ void bounce(const Geo &g, const Phys &ph, const A &ad
     for (int i = 1; i < 9; ++i) {
         if (m & (1u << (i - 1))) {
             C v;
+            constexpr bool NC = (MODE == MODE_TWO_LATTICE);
+            const int sl = bounce_slot<MODE>(i);
             if (MODE == MODE_AA_LOCAL) v = f[i];
-            else v = S::dec(own_value<S, MODE>(raw, own, bounce_slot<MODE>(i), k));
-            if (ph.has_wall) v = v + PC<C>::wt(ph, wall_side(g, ad.gx(k), ad.gy(), i), i);
+            else if (OwnPreload<S, MODE>::value || sl == 0 || sl == 1 || sl == 3)
+                v = S::dec_step(own_value<S, MODE>(raw, own, sl, k));
+            else
+                v = S::dec_step(ld1<NC>(src + ad.eidx(sl, k, 0, 0)));
+            if (ph.has_wall) v = v + PC<C>::wt(ph, wall_side(g, ad.gx(k), ad.gy(), i), i) * C(S::SCALE);
             f[i] = v;
         }
     }
@@ -687,7 +717,7 @@ __device__ __forceinline__ void load_force(const Geo &g, const Phys &ph, const A
 }
 
 template <class S, class A, int MODE, bool HAS_MASK, int FORCE, int K>
-__device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad,
+__device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                         const V16<typename S::R, S::VEC> own[9],
                                         unsigned long long mv, const V16<typename S::R, S::VEC> raw[9],
                                         const typename S::R edge[9], const typename S::C Fx[],
@@ -702,8 +732,8 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
         for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(C(0));
         return;
     }
-    if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, raw, own, K, m, f);
-    collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC)>(f, Fx[K], Fy[K], co);
+    if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, src, raw, own, K, m, f);
+    collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE>(f, Fx[K], Fy[K], co);
     if constexpr (S::STOCHASTIC) {
         unsigned h = fmix32((unsigned)ad.node(K) ^ tseed);
 #pragma unroll
@@ -720,7 +750,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
 // Nodes K0 .. K1-1 of the thread, in order (compile-time unrolled).
 template <class S, class A, int MODE, bool HAS_MASK, int FORCE, int K, int K1>
 struct NodeRange {
-    static __device__ __forceinline__ void run(const Geo &g, const Phys &ph, const A &ad,
+    static __device__ __forceinline__ void run(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                                const V16<typename S::R, S::VEC> own[9],
                                                unsigned long long mv,
                                                const V16<typename S::R, S::VEC> raw[9],
@@ -728,9 +758,9 @@ struct NodeRange {
                                                const typename S::C Fy[], const Coef<typename S::C> &co,
                                                unsigned tseed, V16<typename S::R, S::VEC> out[9]) {
         if constexpr (K < K1) {
-            do_node<S, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, tseed, out);
-            NodeRange<S, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, tseed,
-                                                                   out);
+            do_node<S, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed, out);
+            NodeRange<S, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co,
+                                                                   tseed, out);
         }
     }
 };
@@ -804,7 +834,8 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
     gather_raw<S, MODE>(ad, src, active, lane, mv, raw, edge);
     if (!active) return; // no collective operation follows
     V16<R, VEC> own[9];
-    if (HAS_MASK && MODE != MODE_AA_LOCAL && mv != 0ull) preload_own<S, MODE>(ad, src, mv, own);
+    if (HAS_MASK && MODE != MODE_AA_LOCAL && OwnPreload<S, MODE>::value && mv != 0ull)
+        preload_own<S, MODE>(ad, src, mv, own);
 
     C Fx[VEC], Fy[VEC];
     load_force<S, FORCE>(g, ph, ad, active, Fx, Fy);
@@ -812,7 +843,7 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
 
     V16<R, VEC> out[9];
     const unsigned tseed = S::STOCHASTIC ? fmix32(step * 0x9E3779B9u + 0x632BE5ABu) : 0u;
-    NodeRange<S, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, own, mv, raw, edge, Fx, Fy, co, tseed, out);
+    NodeRange<S, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed, out);
     store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
 }
 
@@ -881,7 +912,7 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
         if (m != 0xFFu) {                                                                 \
             C f[9];                                                                       \
             node_values<S, ((K) < VEC ? (K) : 0), MODE_TWO_LATTICE>(raw, edge, f);        \
-            if (m != 0u) bounce<S, MODE_TWO_LATTICE>(g, ph, ad, raw, own, (K), m, f);     \
+            if (m != 0u) bounce<S, MODE_TWO_LATTICE>(g, ph, ad, src, raw, own, (K), m, f);\
             C l[9], gg[9];                                                                \
             for (int j = 0; j < 9; ++j) l[j] = lam[j][(K)];                               \
             adjoint_node<C, FORCE != FORCE_NONE>(f, l, Fx[(K)], Fy[(K)], omega, gg,       \
@@ -1353,22 +1384,31 @@ static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, vo
     }
     return cudaGetLastError();
 }
-template <int P, class A, int MODE, bool HM>
+// Dense (TILED false) or tiled addressing with the vector width of the step
+// kind, the force mode and the mask flag.
+template <int P, bool TILED, int MODE, bool HM, int F>
+static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
+                            cudaStream_t s) {
+    constexpr int V = StepVec<P, HM, MODE, F>::value;
+    typedef typename std::conditional<TILED, TileAddr<V>, DenseAddr<V>>::type A;
+    return step_launch<P, A, MODE, HM, F>(g, ph, src, dst, t, r, s);
+}
+template <int P, bool TILED, int MODE, bool HM>
 static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                               cudaStream_t s) {
     switch (ph.force_mode) {
-    case FORCE_NONE: return step_launch<P, A, MODE, HM, FORCE_NONE>(g, ph, src, dst, t, r, s);
-    case FORCE_UNIFORM: return step_launch<P, A, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, t, r, s);
-    default: return step_launch<P, A, MODE, HM, FORCE_FIELD>(g, ph, src, dst, t, r, s);
+    case FORCE_NONE: return step_vec<P, TILED, MODE, HM, FORCE_NONE>(g, ph, src, dst, t, r, s);
+    case FORCE_UNIFORM: return step_vec<P, TILED, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, t, r, s);
+    default: return step_vec<P, TILED, MODE, HM, FORCE_FIELD>(g, ph, src, dst, t, r, s);
     }
 }
-template <int P, class A, bool HM>
+template <int P, bool TILED, bool HM>
 static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned t, Rows r,
                              cudaStream_t s) {
     switch (mode) {
-    case MODE_TWO_LATTICE: return step_force<P, A, MODE_TWO_LATTICE, HM>(g, ph, src, dst, t, r, s);
-    case MODE_AA_PULLPUSH: return step_force<P, A, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, t, r, s);
-    default: return step_force<P, A, MODE_AA_LOCAL, HM>(g, ph, src, dst, t, r, s);
+    case MODE_TWO_LATTICE: return step_force<P, TILED, MODE_TWO_LATTICE, HM>(g, ph, src, dst, t, r, s);
+    case MODE_AA_PULLPUSH: return step_force<P, TILED, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, t, r, s);
+    default: return step_force<P, TILED, MODE_AA_LOCAL, HM>(g, ph, src, dst, t, r, s);
     }
 }
 
@@ -1380,19 +1420,18 @@ static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void 
 template <int P>
 cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned long long t,
                         cudaStream_t s) {
-    constexpr int VM = StepVec<P, true>::value, VN = StepVec<P, false>::value;
     const unsigned tt = (unsigned)t;
     const Rows all = {0, g.ny, 1};
     if (g.layout == LBM_DENSE) {
         if (g.has_mask && g.frame_y) {
-            cudaError_t e = step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, tt, Rows{0, 2, g.ny - 1}, s);
+            cudaError_t e = step_mode<P, false, true>(g, ph, mode, src, dst, tt, Rows{0, 2, g.ny - 1}, s);
             if (e != cudaSuccess) return e;
-            return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, tt, Rows{1, g.ny - 2, 1}, s);
+            return step_mode<P, false, false>(g, ph, mode, src, dst, tt, Rows{1, g.ny - 2, 1}, s);
         }
-        if (g.has_mask) return step_mode<P, DenseAddr<VM>, true>(g, ph, mode, src, dst, tt, all, s);
-        return step_mode<P, DenseAddr<VN>, false>(g, ph, mode, src, dst, tt, all, s);
+        if (g.has_mask) return step_mode<P, false, true>(g, ph, mode, src, dst, tt, all, s);
+        return step_mode<P, false, false>(g, ph, mode, src, dst, tt, all, s);
     }
-    return step_mode<P, TileAddr<VM>, true>(g, ph, mode, src, dst, tt, all, s);
+    return step_mode<P, true, true>(g, ph, mode, src, dst, tt, all, s);
 }
 
 static inline dim3 node_blocks(const Geo &g) {
