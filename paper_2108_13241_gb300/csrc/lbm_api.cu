@@ -87,13 +87,13 @@ struct Plan {
     int ntiles, ntx, nty;
     bool has_mask;
     long long nslot;
-    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_open, total;
+    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, total;
     size_t lat_bytes, mask_bytes;
 };
 
 // Geometry tables and the workspace layout for p.
 void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int32_t> &tile_id,
-               std::vector<int32_t> &nbr, std::vector<int32_t> &txy, std::vector<int4> &open, Plan &pl) {
+               std::vector<int32_t> &nbr, std::vector<int32_t> &txy, Plan &pl) {
     const long long N = (long long)p.nx * p.ny;
     mask.assign((size_t)N, 0);
     pl.nfluid = build_link_mask(p, mask.data());
@@ -133,9 +133,6 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
     off += align256((size_t)RED_BLOCKS * 4 * sizeof(double));
     pl.off_out = off;
     off += align256(4 * sizeof(double));
-    build_open_nodes(p, mask.data(), open);
-    pl.off_open = off;
-    off += align256(open.size() * sizeof(int4));
     pl.total = off;
 }
 
@@ -197,9 +194,8 @@ lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes) {
     if (!bytes || check_params(p)) return LBM_ERR_INVALID;
     std::vector<uint8_t> mask;
     std::vector<int32_t> tid, nbr, txy;
-    std::vector<int4> open;
     Plan pl;
-    make_plan(*p, mask, tid, nbr, txy, open, pl);
+    make_plan(*p, mask, tid, nbr, txy, pl);
     if (9ll * pl.nslot >= (1ll << 32)) return LBM_ERR_INVALID;
     *bytes = pl.total;
     return LBM_OK;
@@ -216,9 +212,8 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     c->stream = (cudaStream_t)p->stream;
     c->sticky = LBM_OK;
     std::vector<int32_t> txy;
-    std::vector<int4> open;
     Plan pl;
-    make_plan(*p, c->mask, c->tile_id, c->nbr, txy, open, pl);
+    make_plan(*p, c->mask, c->tile_id, c->nbr, txy, pl);
     if (9ll * pl.nslot >= (1ll << 32)) {
         delete c;
         return LBM_ERR_INVALID;
@@ -260,8 +255,6 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
         g.frame_y = inner_free;
     }
     g.mask = pl.mask_bytes ? reinterpret_cast<const uint8_t *>(ws + pl.off_mask) : nullptr;
-    g.nopen = (int)open.size();
-    g.open_nodes = open.empty() ? nullptr : reinterpret_cast<const int4 *>(ws + pl.off_open);
 
     Phys &ph = c->phys;
     std::memset(&ph, 0, sizeof(ph));
@@ -311,9 +304,6 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     st = cuda_check(c, cudaMemsetAsync(c->lat[0], 0, pl.lat_bytes, s), "memset lattice");
     if (!st && p->pattern == LBM_TWO_LATTICE)
         st = cuda_check(c, cudaMemsetAsync(c->lat[1], 0, pl.lat_bytes, s), "memset lattice");
-    if (!st && !open.empty())
-        st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_open, open.data(), open.size() * sizeof(int4),
-                                           cudaMemcpyHostToDevice, s), "copy open-side nodes");
     if (!st && p->layout == LBM_DENSE && pl.mask_bytes)
         st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_mask, c->mask.data(), pl.mask_bytes,
                                            cudaMemcpyHostToDevice, s), "copy mask");
@@ -399,11 +389,6 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     const Geo &g = ctx->geo;
     for (int k = 0; k < n; ++k) {
         cudaError_t e;
-        if (g.nopen) {
-            e = LBM_DISPATCH(ctx->p.precision, launch_open<P>(g, ctx->phys, current_phase(ctx),
-                                                              current_lattice(ctx), ctx->stream));
-            if (e != cudaSuccess) return cuda_check(ctx, e, "open-side kernel");
-        }
         if (ctx->p.pattern == LBM_TWO_LATTICE) {
             const void *a = ctx->lat[ctx->cur];
             void *b = ctx->lat[1 - ctx->cur];
@@ -520,14 +505,9 @@ lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long l
     for (int k = 0; k < n; ++k) {
         if (!h_states[k] || !h_states[k + 1] || ((uintptr_t)h_states[k] & 15) || ((uintptr_t)h_states[k + 1] & 15))
             return fail(ctx, LBM_ERR_INVALID, "bad state pointer");
-        cudaError_t e = cudaSuccess;
-        if (ctx->geo.nopen)
-            e = LBM_DISPATCH(ctx->p.precision, launch_open<P>(ctx->geo, ctx->phys, PH_PLAIN, h_states[k],
-                                                              ctx->stream));
-        if (e == cudaSuccess)
-            e = LBM_DISPATCH(ctx->p.precision,
-                             launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE, h_states[k], h_states[k + 1],
-                                            (unsigned long long)(t0 + k), ctx->stream));
+        cudaError_t e = LBM_DISPATCH(ctx->p.precision,
+                                     launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE, h_states[k],
+                                                    h_states[k + 1], (unsigned long long)(t0 + k), ctx->stream));
         if (e != cudaSuccess) return cuda_check(ctx, e, "forward_states kernel");
     }
     return LBM_OK;
@@ -593,9 +573,8 @@ lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id
     if (check_params(p)) return LBM_ERR_INVALID;
     std::vector<uint8_t> mask;
     std::vector<int32_t> tid, nbr, txy;
-    std::vector<int4> open;
     Plan pl;
-    make_plan(*p, mask, tid, nbr, txy, open, pl);
+    make_plan(*p, mask, tid, nbr, txy, pl);
     if (h_mask) std::memcpy(h_mask, mask.data(), mask.size());
     if (p->layout == LBM_SPARSE_TILE16) {
         if (h_tile_id) std::memcpy(h_tile_id, tid.data(), tid.size() * 4);

@@ -33,36 +33,7 @@ bool pull_source(const lbm_params &p, int x, int y, int i, long long *src) {
     return true;
 }
 
-// Side crossed by link i of node (x, y) when x - c_i is not a lattice node
-// (0 west, 1 east, 2 south, 3 north; the y side first), else -1.
-int crossed_side(const lbm_params &p, int x, int y, int i) {
-    const int sy = y - kCy[i];
-    if ((sy < 0 || sy >= p.ny) && !p.south.periodic) return sy < 0 ? 2 : 3;
-    const int sx = x - kCx[i];
-    if ((sx < 0 || sx >= p.nx) && !p.west.periodic) return sx < 0 ? 0 : 1;
-    return -1;
-}
-
 } // namespace
-
-void build_open_nodes(const lbm_params &p, const uint8_t *mask, std::vector<int4> &out) {
-    out.clear();
-    const lbm_side *sides[4] = {&p.west, &p.east, &p.south, &p.north};
-    for (int s = 0; s < 4; ++s) {
-        if (sides[s]->periodic || sides[s]->kind == LBM_SIDE_WALL) continue;
-        const int len = s < 2 ? p.ny : p.nx;
-        for (int k = 0; k < len; ++k) {
-            const int x = s == 0 ? 0 : (s == 1 ? p.nx - 1 : k);
-            const int y = s == 2 ? 0 : (s == 3 ? p.ny - 1 : k);
-            const uint8_t m = mask[(long long)y * p.nx + x];
-            if (m == 0xFF) continue;
-            bool any = false;
-            for (int i = 1; i < 9 && !any; ++i)
-                any = ((m >> (i - 1)) & 1) && crossed_side(p, x, y, i) == s;
-            if (any) out.push_back(make_int4(x, y, s, 0));
-        }
-    }
-}
 
 long long build_link_mask(const lbm_params &p, uint8_t *mask) {
     long long fluid = 0;

@@ -48,8 +48,6 @@ struct Geo {
     const int32_t *tile_id;// sparse [nty][ntx]
     int has_mask;          // 0: every node fluid, both axes periodic
     int frame_y;           // dense, ny >= 3, bounced links only in rows 0 and ny-1
-    int nopen;             // boundary nodes of open sides
-    const int4 *open_nodes;// [nopen]: (x, y, side, 0)
 };
 
 // Physics as the kernels see it.
@@ -97,12 +95,6 @@ template <int P> cudaError_t launch_macros(const Geo &g, const Phys &ph, int pha
 template <int P> cudaError_t launch_reduce(const Geo &g, const Phys &ph, int phase, int kind,
                                            const void *lat, const void *target,
                                            double *partial, double *out, cudaStream_t s);
-// Open sides, before each step on the lattice the step will read (phase of
-// the current state): the boundary nodes' links that pull from beyond an
-// open side get their open-side values, written where the step reads a
-// bounced link.
-template <int P> cudaError_t launch_open(const Geo &g, const Phys &ph, int phase, void *lat,
-                                         cudaStream_t s);
 template <int P> cudaError_t launch_adjoint(const Geo &g, const Phys &ph, const void *state,
                                             const void *lam_in, void *lam_out,
                                             void *grad_force, cudaStream_t s);
@@ -115,10 +107,6 @@ template <int P> cudaError_t launch_macros_adjoint(const Geo &g, const Phys &ph,
 // Link mask: bit (i-1) set iff link i pulls from a solid node or across a
 // wall; 0xFF for solid nodes and for fluid nodes with no link to any node.
 long long build_link_mask(const lbm_params &p, uint8_t *mask);
-// Boundary nodes of open sides: (x, y, side, 0) for every node on an open
-// side's row or column that is not 0xFF and has a link pulling from beyond
-// that side (corner rule: the south/north side decides first).
-void build_open_nodes(const lbm_params &p, const uint8_t *mask, std::vector<int4> &out);
 // Tile map (16x16): tile_id[nty][ntx] (-1 absent), nbr[ntiles][9],
 // tile_xy[ntiles].  Returns the number of kept tiles.
 int build_tile_map(const lbm_params &p, const uint8_t *mask, int32_t *tile_id,

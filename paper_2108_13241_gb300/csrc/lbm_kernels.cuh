@@ -547,6 +547,82 @@ __device__ __forceinline__ void adjoint_node(const C f[9], const C lam[9], C Fx,
     dFy = C(0.5) * Vy * inv + gy;
 }
 
+// ------------------------------------------------------------- open sides
+
+// Open side `side` at boundary node (x, y) (Zou & He, for any side): the
+// links of mask m that pull from beyond the side are unknown; the known
+// shifted values f' fix rho (1 + u.n) = 1 + sum_{c.n=0} f'_j + 2 sum_{c.n>0} f'_j
+// (the weights of those links sum to 1), with u given (velocity side) or rho
+// given and u = (u.n) n (pressure side); then
+//   f'_i = f'_opp(i) + 6 w_i rho (c_i . u) - (c_i . t) N_t,
+//   N_t = 1/2 sum_{c.n=0} (c_j . t) f'_j - rho (u . t)/3.
+// f in units of SC (f - w times SC, as in the step kernel).  Returns the set
+// of links it wrote (bit i).
+template <class C, int SC = 1>
+__device__ unsigned open_side(const Geo &g, const Phys &ph, int x, int y, int side, unsigned m, C f[9]) {
+    unsigned unk = 0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        if (((m >> (i - 1)) & 1u) && wall_side(g, x, y, i) == side) unk |= 1u << i;
+    if (!unk) return 0u;
+    const int nx_ = side == 0 ? -1 : (side == 1 ? 1 : 0), ny_ = side == 2 ? -1 : (side == 3 ? 1 : 0);
+    const int tx = nx_ == 0, ty = ny_ == 0;
+    C d = C(0), st = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cn = cx(i) * nx_ + cy(i) * ny_;
+        if (cn == 0) {
+            d += f[i];
+            st += C(cx(i) * tx + cy(i) * ty) * f[i];
+        } else if (cn > 0) {
+            d += C(2) * f[i];
+        }
+    }
+    const int k = side < 2 ? y : x, len = side < 2 ? g.ny : g.nx;
+    const C *val = reinterpret_cast<const C *>(ph.open_val[side]);
+    C rho, ux, uy;
+    if (ph.open_kind[side] == LBM_SIDE_VELOCITY) {
+        if (val) {
+            ux = val[k];
+            uy = val[len + k];
+        } else if constexpr (sizeof(C) == 8) {
+            ux = ph.open_u[side][0];
+            uy = ph.open_u[side][1];
+        } else {
+            ux = ph.open_u_f[side][0];
+            uy = ph.open_u_f[side][1];
+        }
+        rho = (C(1) + d * C(1.0 / SC)) / (C(1) + (C(nx_) * ux + C(ny_) * uy));
+    } else {
+        if (val) rho = val[k];
+        else if constexpr (sizeof(C) == 8) rho = ph.open_rho[side];
+        else rho = ph.open_rho_f[side];
+        const C un = (C(1) + d * C(1.0 / SC) - rho) / rho;
+        ux = C(nx_) * un;
+        uy = C(ny_) * un;
+    }
+    const C rs = rho * C(SC);
+    const C Nt = C(0.5) * st - rs * (C(tx) * ux + C(ty) * uy) * C(1.0 / 3.0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        if ((unk >> i) & 1u)
+            f[i] = f[opp(i)] + C(6) * wgt<C>(i) * rs * (C(cx(i)) * ux + C(cy(i)) * uy) -
+                   C(cx(i) * tx + cy(i) * ty) * Nt;
+    return unk;
+}
+
+// Every open side whose row or column holds (x, y).
+template <class C, int SC = 1>
+__device__ __forceinline__ void apply_open(const Geo &g, const Phys &ph, int x, int y, unsigned m, C f[9]) {
+    if (!ph.has_open || m == 0u) return;
+    const bool on[4] = {x == 0, x == g.nx - 1, y == 0, y == g.ny - 1};
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (ph.open_kind[s] != LBM_SIDE_WALL && on[s]) open_side<C, SC>(g, ph, x, y, s, m, f);
+}
+
+
+
 // ------------------------------------------------------------- step kernel
 
 // Gather of the aligned vectors (and the one edge value per x-shifted slot)
@@ -716,7 +792,7 @@ __device__ __forceinline__ void load_force(const Geo &g, const Phys &ph, const A
     }
 }
 
-template <class S, class A, int MODE, bool HAS_MASK, int FORCE, int K>
+template <class S, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, int K>
 __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                         const V16<typename S::R, S::VEC> own[9],
                                         unsigned long long mv, const V16<typename S::R, S::VEC> raw[9],
@@ -733,6 +809,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
         return;
     }
     if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, src, raw, own, K, m, f);
+    if constexpr (OPEN) apply_open<C, S::SCALE>(g, ph, ad.gx(K), ad.gy(), m, f);
     collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE>(f, Fx[K], Fy[K], co);
     if constexpr (S::STOCHASTIC) {
         unsigned h = fmix32((unsigned)ad.node(K) ^ tseed);
@@ -748,7 +825,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
 }
 
 // Nodes K0 .. K1-1 of the thread, in order (compile-time unrolled).
-template <class S, class A, int MODE, bool HAS_MASK, int FORCE, int K, int K1>
+template <class S, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, int K, int K1>
 struct NodeRange {
     static __device__ __forceinline__ void run(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                                const V16<typename S::R, S::VEC> own[9],
@@ -758,9 +835,10 @@ struct NodeRange {
                                                const typename S::C Fy[], const Coef<typename S::C> &co,
                                                unsigned tseed, V16<typename S::R, S::VEC> out[9]) {
         if constexpr (K < K1) {
-            do_node<S, A, MODE, HAS_MASK, FORCE, K>(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed, out);
-            NodeRange<S, A, MODE, HAS_MASK, FORCE, K + 1, K1>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co,
-                                                                   tseed, out);
+            do_node<S, A, MODE, HAS_MASK, FORCE, OPEN, K>(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed,
+                                                          out);
+            NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, K + 1, K1>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy,
+                                                                         co, tseed, out);
         }
     }
 };
@@ -812,7 +890,7 @@ template <int P, bool HAS_MASK> struct MinBlocks {
     enum { value = P == LBM_F64 ? 1 : ((HAS_MASK && P == LBM_F16S) ? 3 : 4) };
 };
 
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE>
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN>
 __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
     k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0, int ystride, unsigned step) {
     typedef StV<P, A::VEC_> S;
@@ -843,7 +921,8 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
 
     V16<R, VEC> out[9];
     const unsigned tseed = S::STOCHASTIC ? fmix32(step * 0x9E3779B9u + 0x632BE5ABu) : 0u;
-    NodeRange<S, A, MODE, HAS_MASK, FORCE, 0, VEC>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed, out);
+    NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, 0, VEC>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed,
+                                                             out);
     store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
 }
 
@@ -1031,76 +1110,6 @@ __device__ __forceinline__ void gather_node(const Geo &g, const Phys &ph, int ph
     }
 }
 
-// Open side `side` at boundary node (x, y) (Zou & He, for any side): the
-// links of mask m that pull from beyond the side are unknown; the known
-// shifted values f' fix rho (1 + u.n) = 1 + sum_{c.n=0} f'_j + 2 sum_{c.n>0} f'_j
-// (the weights of those links sum to 1), with u given (velocity side) or rho
-// given and u = (u.n) n (pressure side); then
-//   f'_i = f'_opp(i) + 6 w_i rho (c_i . u) - (c_i . t) N_t,
-//   N_t = 1/2 sum_{c.n=0} (c_j . t) f'_j - rho (u . t)/3.
-// Returns the set of links it wrote (bit i).
-template <class C>
-__device__ unsigned open_side(const Geo &g, const Phys &ph, int x, int y, int side, unsigned m, C f[9]) {
-    unsigned unk = 0;
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-        if (((m >> (i - 1)) & 1u) && wall_side(g, x, y, i) == side) unk |= 1u << i;
-    if (!unk) return 0u;
-    const int nx_ = side == 0 ? -1 : (side == 1 ? 1 : 0), ny_ = side == 2 ? -1 : (side == 3 ? 1 : 0);
-    const int tx = nx_ == 0, ty = ny_ == 0;
-    C d = C(0), st = C(0);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cn = cx(i) * nx_ + cy(i) * ny_;
-        if (cn == 0) {
-            d += f[i];
-            st += C(cx(i) * tx + cy(i) * ty) * f[i];
-        } else if (cn > 0) {
-            d += C(2) * f[i];
-        }
-    }
-    const int k = side < 2 ? y : x, len = side < 2 ? g.ny : g.nx;
-    const C *val = reinterpret_cast<const C *>(ph.open_val[side]);
-    C rho, ux, uy;
-    if (ph.open_kind[side] == LBM_SIDE_VELOCITY) {
-        if (val) {
-            ux = val[k];
-            uy = val[len + k];
-        } else if constexpr (sizeof(C) == 8) {
-            ux = ph.open_u[side][0];
-            uy = ph.open_u[side][1];
-        } else {
-            ux = ph.open_u_f[side][0];
-            uy = ph.open_u_f[side][1];
-        }
-        rho = (C(1) + d) / (C(1) + (C(nx_) * ux + C(ny_) * uy));
-    } else {
-        if (val) rho = val[k];
-        else if constexpr (sizeof(C) == 8) rho = ph.open_rho[side];
-        else rho = ph.open_rho_f[side];
-        const C un = (C(1) + d - rho) / rho;
-        ux = C(nx_) * un;
-        uy = C(ny_) * un;
-    }
-    const C Nt = C(0.5) * st - rho * (C(tx) * ux + C(ty) * uy) * C(1.0 / 3.0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-        if ((unk >> i) & 1u)
-            f[i] = f[opp(i)] + C(6) * wgt<C>(i) * rho * (C(cx(i)) * ux + C(cy(i)) * uy) -
-                   C(cx(i) * tx + cy(i) * ty) * Nt;
-    return unk;
-}
-
-// Every open side whose row or column holds (x, y).
-template <class C>
-__device__ __forceinline__ void apply_open(const Geo &g, const Phys &ph, int x, int y, unsigned m, C f[9]) {
-    if (!ph.has_open || m == 0u) return;
-    const bool on[4] = {x == 0, x == g.nx - 1, y == 0, y == g.ny - 1};
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-        if (ph.open_kind[s] != LBM_SIDE_WALL && on[s]) open_side<C>(g, ph, x, y, s, m, f);
-}
-
 template <class C>
 __device__ __forceinline__ void node_force(const Geo &g, const Phys &ph, long long n, C &Fx, C &Fy) {
     if (ph.force_mode == FORCE_FIELD) {
@@ -1277,28 +1286,6 @@ __global__ void __launch_bounds__(AUX_BLOCK) k_reduce_final(const double *partia
     block_sum4(acc, out);
 }
 
-// Open sides, before a step: each boundary node's links that pull from beyond
-// its open side get their open-side values, stored where the step reads a
-// bounced link (own slot opp(i) in the plain phase, own slot i in the AA
-// phases).  Only the node's own bounce reads those slots, and the step
-// overwrites them, so the state between steps stays canonical.
-template <int P>
-__global__ void k_open(const Geo g, const Phys ph, int phase, void *lat_v) {
-    typedef St<P> S;
-    typedef typename S::C C;
-    const int e = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (e >= g.nopen) return;
-    const int4 b = g.open_nodes[e];
-    const unsigned m = node_mask(g, b.x, b.y);
-    typename S::R *M = reinterpret_cast<typename S::R *>(lat_v);
-    C f[9];
-    gather_node<S>(g, ph, phase, M, b.x, b.y, m, f);
-    const unsigned unk = open_side<C>(g, ph, b.x, b.y, b.z, m, f);
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-        if ((unk >> i) & 1u) M[cidx(g, b.x, b.y, phase == PH_PLAIN ? opp(i) : i)] = S::enc(f[i]);
-}
-
 // Transpose of the macros at the current (two-lattice, dense) state.
 template <int P>
 __global__ void k_macros_adjoint(const Geo g, const Phys ph, const void *state_v, const void *grho_v,
@@ -1371,7 +1358,7 @@ template <int VEC> static Shape step_shape(const Geo &g) {
 struct Rows {
     int row0, nrows, stride;
 };
-template <int P, class A, int MODE, bool HM, int F>
+template <int P, class A, int MODE, bool HM, int F, bool OPEN>
 static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                                cudaStream_t s) {
     const Shape sh = step_shape<A::VEC_>(g);
@@ -1379,7 +1366,7 @@ static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, vo
     const unsigned rows = sh.dense ? (unsigned)r.nrows : 1u;
     for (unsigned k = 0; k < rows; k += 65535u) {
         const unsigned gy = rows - k < 65535u ? rows - k : 65535u;
-        k_step<P, A, MODE, HM, F><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, r.row0 + (int)k * r.stride,
+        k_step<P, A, MODE, HM, F, OPEN><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, r.row0 + (int)k * r.stride,
                                                                     r.stride, t);
     }
     return cudaGetLastError();
@@ -1391,7 +1378,10 @@ static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void 
                             cudaStream_t s) {
     constexpr int V = StepVec<P, HM, MODE, F>::value;
     typedef typename std::conditional<TILED, TileAddr<V>, DenseAddr<V>>::type A;
-    return step_launch<P, A, MODE, HM, F>(g, ph, src, dst, t, r, s);
+    // open sides are only on masked kernels (their links are marked)
+    if constexpr (HM)
+        if (ph.has_open) return step_launch<P, A, MODE, HM, F, true>(g, ph, src, dst, t, r, s);
+    return step_launch<P, A, MODE, HM, F, false>(g, ph, src, dst, t, r, s);
 }
 template <int P, bool TILED, int MODE, bool HM>
 static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
@@ -1437,13 +1427,6 @@ cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src,
 static inline dim3 node_blocks(const Geo &g) {
     const unsigned rows = (unsigned)(g.ny < 65535 ? g.ny : 65535);
     return dim3((unsigned)((g.nx + AUX_BLOCK - 1) / AUX_BLOCK), rows, (unsigned)((g.ny + rows - 1) / rows));
-}
-
-template <int P>
-cudaError_t launch_open(const Geo &g, const Phys &ph, int phase, void *lat, cudaStream_t s) {
-    if (g.nopen == 0) return cudaSuccess;
-    k_open<P><<<(g.nopen + 127) / 128, 128, 0, s>>>(g, ph, phase, lat);
-    return cudaGetLastError();
 }
 
 template <int P>
@@ -1514,7 +1497,6 @@ cudaError_t launch_macros_adjoint(const Geo &g, const Phys &ph, const void *stat
     template cudaError_t launch_adjoint<P>(const Geo &, const Phys &, const void *, const void *, void *,  \
                                            void *, cudaStream_t);                                           \
     template cudaError_t launch_macros_adjoint<P>(const Geo &, const Phys &, const void *, const void *,   \
-                                                  const void *, void *, void *, cudaStream_t);              \
-    template cudaError_t launch_open<P>(const Geo &, const Phys &, int, void *, cudaStream_t);
+                                                  const void *, void *, void *, cudaStream_t);
 
 } // namespace lbm
