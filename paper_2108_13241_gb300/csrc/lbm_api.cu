@@ -248,7 +248,9 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     g.nslot = pl.nslot;
     g.nnode = (long long)p->nx * p->ny;
     g.has_mask = pl.has_mask;
-    if (p->layout == LBM_DENSE && pl.has_mask && p->ny >= 3) {
+    // the split costs a second launch (a few microseconds): worth it on large
+    // grids only
+    if (p->layout == LBM_DENSE && pl.has_mask && p->ny >= 3 && (long long)p->nx * p->ny > (1ll << 21)) {
         bool inner_free = true;
         for (size_t n = (size_t)p->nx; n < (size_t)p->nx * (size_t)(p->ny - 1) && inner_free; ++n)
             inner_free = c->mask[n] == 0;

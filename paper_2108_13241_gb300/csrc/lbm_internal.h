@@ -47,7 +47,7 @@ struct Geo {
     const int32_t *tile_xy;// sparse [ntiles]: (ty << 16) | tx
     const int32_t *tile_id;// sparse [nty][ntx]
     int has_mask;          // 0: every node fluid, both axes periodic
-    int frame_y;           // dense, ny >= 3, bounced links only in rows 0 and ny-1
+    int frame_y;           // dense, > 2^21 nodes, bounced links only in rows 0 and ny-1
 };
 
 // Physics as the kernels see it.

@@ -69,3 +69,31 @@ def test_full_size_aa_equals_two_lattice_fp32(L, tgv):
         out.append(sim.get_f())
         del sim
     assert torch.equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("phi", [0.2, 0.8])
+@pytest.mark.parametrize("pattern", ["two_lattice", "aa"])
+def test_porous_full_size_one_step_matches_oracle(L, orc, phi, pattern):
+    """The 4096^2 porous medium (discs r in [8, 32], force 1e-6, periodic x,
+    walls y) in the tiled FP32 layout, as bench.py times it: one GPU step from
+    the GPU's own state against one oracle step from the same state, every
+    fluid node."""
+    solid, _, _ = inputs.porous_discs(N, N, phi, rmin=8, rmax=32)
+    sim = L.LBM(N, N, 0.8, solid=solid, force=(1e-6, 0.0), periodic_y=False, precision="f32",
+                layout="sparse", pattern=pattern)
+    # deviations from rest of order 1e-2, so that the FP32 export w_i + (f_i -
+    # w_i) rounds far below the tolerance (as in the Taylor-Green case)
+    rho, u = inputs.taylor_green(N, N, 0.05)
+    sim.init_equilibrium(rho, u)
+    sim.step(5)
+    A = sim.get_f().double().cpu().numpy()
+    sim.step(1)
+    B = sim.get_f().double().cpu().numpy()
+    s = orc.Setup(nx=N, ny=N, tau=0.8, periodic_x=True, periodic_y=False, force=(1e-6, 0.0))
+    mask, nf = orc.link_mask(s, solid)
+    assert nf == sim.fluid_nodes
+    ref = orc.step(s, mask, A)
+    fl = mask != 0xFF
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None]
+    err = np.linalg.norm(B[:, fl] - ref[:, fl]) / np.linalg.norm(ref[:, fl] - w)
+    assert err <= 1e-5, err

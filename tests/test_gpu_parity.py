@@ -243,9 +243,9 @@ def test_step_count_and_zero_steps(L):
 
 @pytest.mark.parametrize("layout,pattern", VARIANTS)
 @pytest.mark.parametrize("steps", [1, 2, 41])
-def test_wall_rows_split_fp64_matches_oracle(L, orc, layout, pattern, steps):
-    """Periodic x, moving walls in y, no obstacle: the dense layout runs the
-    wall rows with the masked kernel and the other rows without a mask."""
+def test_wall_rows_fp64_matches_oracle(L, orc, layout, pattern, steps):
+    """Periodic x, moving walls in y, no obstacle (small grid: one masked
+    launch)."""
     nx, ny = 64, 24
     case = C.Case("wallrows%dx%d" % (nx, ny), nx, ny, 0.7, px=True, py=False,
                   walls={"south": (0.03, 0.0), "north": (-0.02, 0.0)}, force=(1e-5, -2e-6))
@@ -257,8 +257,33 @@ def test_wall_rows_split_fp64_matches_oracle(L, orc, layout, pattern, steps):
     assert C.rel_l2(g["u"], o["u"]) <= 1e-11
 
 
+@pytest.mark.parametrize("pattern", ["two_lattice", "aa"])
+@pytest.mark.parametrize("steps", [1, 2])
+@pytest.mark.parametrize("sides", ["walls", "open"])
+def test_wall_rows_split_fp64_large_grid(L, orc, pattern, steps, sides):
+    """2048 x 2056 (> 2^21 nodes), periodic x, moving walls (or velocity
+    inlet and pressure outlet) in y, force: the dense layout runs the two
+    boundary rows with the masked kernel and the other rows with the unmasked
+    one; every node against the oracle."""
+    nx, ny = 2048, 2056
+    case = C.Case("wallrows_large_" + sides, nx, ny, 0.7, px=True, py=False,
+                  walls={"south": (0.03, 0.0), "north": (-0.02, 0.0)}, force=(1e-5, -2e-6))
+    if sides == "open":
+        case.walls = {}
+        case.open = {"south": ("velocity", (0.01, 0.02)), "north": ("pressure", 1.0)}
+    y = np.arange(ny)[:, None]
+    x = np.arange(nx)[None, :]
+    case.rho0 = 1.0 + 0.01 * np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * y / ny)
+    case.u0 = np.stack([0.03 * np.cos(2 * np.pi * y / ny) + 0 * x, 0.02 * np.sin(2 * np.pi * x / nx) + 0 * y])
+    o = run_oracle(orc, case, steps)
+    g = run_gpu(L, case, steps, "f64", "dense", pattern)
+    assert C.rel_l2(g["f"], o["f"]) <= 1e-12
+    ref = run_gpu(L, case, steps, "f64", "sparse", pattern)
+    assert np.array_equal(g["f"], ref["f"])
+
+
 @pytest.mark.parametrize("precision,tol", [("f32", 1e-5), ("f16s", 5e-3)])
-def test_wall_rows_split_low_precision(L, orc, precision, tol):
+def test_wall_rows_low_precision(L, orc, precision, tol):
     nx, ny = 128, 64
     fx, rho, u = inputs.poiseuille(nx, ny, 0.8, 0.05)
     case = C.Case("pois%dx%d" % (nx, ny), nx, ny, 0.8, px=True, py=False, force=(fx, 0.0))
