@@ -125,7 +125,7 @@ template <int P, int V> struct StV : St<P> {
 // without a force field moves 4 (bounced values loaded on demand).
 template <int P, bool HAS_MASK, int MODE = MODE_AA_PULLPUSH, int FORCE = FORCE_NONE> struct StepVec {
     enum {
-        value = (P == LBM_F32 && HAS_MASK && (MODE != MODE_TWO_LATTICE || FORCE == FORCE_FIELD)) ? 2 : St<P>::VEC
+        value = (P == LBM_F32 && HAS_MASK && (MODE == MODE_AA_PULLPUSH || FORCE == FORCE_FIELD)) ? 2 : St<P>::VEC
     };
 };
 // Whether the step preloads the own-node vectors its bounced links read
