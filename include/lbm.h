@@ -260,6 +260,11 @@ lbm_status lbm_reduce_f_noalloc(lbm_precision precision, const void *d_f, const 
 
 long long lbm_fluid_nodes(const lbm_ctx *ctx);
 long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Kernel launches of one lbm_step time step (1 for most configurations; 2
+ * when the dense grid runs its boundary rows with the masked kernel and the
+ * rest without, more for grids of over 65535 rows).  -1 for a NULL ctx. */
+int lbm_launches_per_step(const lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status s);
 const char *lbm_last_error(const lbm_ctx *ctx);
 

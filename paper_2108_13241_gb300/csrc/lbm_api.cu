@@ -591,6 +591,13 @@ lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id
 
 long long lbm_fluid_nodes(const lbm_ctx *ctx) { return ctx ? ctx->nfluid : -1; }
 long long lbm_step_count(const lbm_ctx *ctx) { return ctx ? ctx->steps : -1; }
+int lbm_launches_per_step(const lbm_ctx *ctx) {
+    if (!ctx) return -1;
+    const Geo &g = ctx->geo;
+    if (g.layout != LBM_DENSE) return 1;
+    if (g.has_mask && g.frame_y) return 1 + (g.ny - 2 + 65534) / 65535;
+    return (g.ny + 65534) / 65535;
+}
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 
 } // extern "C"

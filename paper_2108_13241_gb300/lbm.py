@@ -101,6 +101,7 @@ def _load():
         "lbm_reduce_f_noalloc": ([ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp], st),
         "lbm_fluid_nodes": ([_vp], ctypes.c_longlong),
         "lbm_step_count": ([_vp], ctypes.c_longlong),
+        "lbm_launches_per_step": ([_vp], ctypes.c_int),
         "lbm_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lbm_last_error": ([_vp], ctypes.c_char_p),
     }
@@ -392,6 +393,10 @@ class LBM:
     @property
     def steps(self) -> int:
         return lbm_step_count(self.ctx)
+
+    @property
+    def launches_per_step(self) -> int:
+        return _load().lbm_launches_per_step(self.ctx)
 
     def _t(self, a, shape):
         t = torch.as_tensor(a, dtype=self.dtype, device=self.device).contiguous()
