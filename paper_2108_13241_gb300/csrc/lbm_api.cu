@@ -87,13 +87,37 @@ struct Plan {
     int ntiles, ntx, nty;
     bool has_mask;
     long long nslot;
-    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, total;
+    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_list2, off_list4, total;
     size_t lat_bytes, mask_bytes;
+    bool use_list;
 };
+
+// Sparse layout: tile masks [ntiles][256] and the lists of vectors of 2 and
+// of 4 nodes (along a tile row) that hold a fluid node, entry t * TPT + k for
+// the k-th vector of tile t (TPT = 128 or 64), in tile order.
+struct SparseTables {
+    std::vector<uint8_t> tmask;
+    std::vector<uint32_t> list2, list4;
+};
+
+void build_vector_lists(int ntiles, const std::vector<uint8_t> &tmask, SparseTables &st) {
+    for (int vec = 2; vec <= 4; vec += 2) {
+        std::vector<uint32_t> &out = vec == 2 ? st.list2 : st.list4;
+        out.clear();
+        const int tpt = TILE_N / vec;
+        for (int t = 0; t < ntiles; ++t)
+            for (int k = 0; k < tpt; ++k) {
+                const uint8_t *m = &tmask[(size_t)t * TILE_N + (size_t)k * vec];
+                bool fluid = false;
+                for (int j = 0; j < vec; ++j) fluid = fluid || m[j] != 0xFF;
+                if (fluid) out.push_back((uint32_t)t * (uint32_t)tpt + (uint32_t)k);
+            }
+    }
+}
 
 // Geometry tables and the workspace layout for p.
 void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int32_t> &tile_id,
-               std::vector<int32_t> &nbr, std::vector<int32_t> &txy, Plan &pl) {
+               std::vector<int32_t> &nbr, std::vector<int32_t> &txy, SparseTables &sp, Plan &pl) {
     const long long N = (long long)p.nx * p.ny;
     mask.assign((size_t)N, 0);
     pl.nfluid = build_link_mask(p, mask.data());
@@ -111,6 +135,9 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
         nbr.resize((size_t)pl.ntiles * 9);
         pl.has_mask = true;
         pl.nslot = (long long)pl.ntiles * TILE_N;
+        sp.tmask.assign((size_t)pl.ntiles * TILE_N, 0xFF);
+        if (pl.ntiles > 0) build_tile_masks(p, mask.data(), txy.data(), pl.ntiles, sp.tmask.data());
+        build_vector_lists(pl.ntiles, sp.tmask, sp);
     } else {
         pl.has_mask = any;
         pl.nslot = N;
@@ -133,6 +160,14 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
     off += align256((size_t)RED_BLOCKS * 4 * sizeof(double));
     pl.off_out = off;
     off += align256(4 * sizeof(double));
+    // the list pays off when a good part of the kept tiles' vectors is solid
+    // (measured on 4096^2 disc media: +10-33% at 42% active vectors, -3% at 87%)
+    pl.use_list = p.layout == LBM_SPARSE_TILE16 && pl.ntiles > 0 &&
+                  (double)sp.list4.size() < 0.85 * (double)pl.ntiles * (TILE_N / 4);
+    pl.off_list2 = off;
+    if (pl.use_list) off += align256(sp.list2.size() * 4);
+    pl.off_list4 = off;
+    if (pl.use_list) off += align256(sp.list4.size() * 4);
     pl.total = off;
 }
 
@@ -194,8 +229,9 @@ lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes) {
     if (!bytes || check_params(p)) return LBM_ERR_INVALID;
     std::vector<uint8_t> mask;
     std::vector<int32_t> tid, nbr, txy;
+    SparseTables sp;
     Plan pl;
-    make_plan(*p, mask, tid, nbr, txy, pl);
+    make_plan(*p, mask, tid, nbr, txy, sp, pl);
     if (9ll * pl.nslot >= (1ll << 32)) return LBM_ERR_INVALID;
     *bytes = pl.total;
     return LBM_OK;
@@ -212,8 +248,9 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     c->stream = (cudaStream_t)p->stream;
     c->sticky = LBM_OK;
     std::vector<int32_t> txy;
+    SparseTables sp;
     Plan pl;
-    make_plan(*p, c->mask, c->tile_id, c->nbr, txy, pl);
+    make_plan(*p, c->mask, c->tile_id, c->nbr, txy, sp, pl);
     if (9ll * pl.nslot >= (1ll << 32)) {
         delete c;
         return LBM_ERR_INVALID;
@@ -309,11 +346,9 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     if (!st && p->layout == LBM_DENSE && pl.mask_bytes)
         st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_mask, c->mask.data(), pl.mask_bytes,
                                            cudaMemcpyHostToDevice, s), "copy mask");
-    std::vector<uint8_t> tmask;
     std::vector<int32_t> nbr3;
+    const std::vector<uint8_t> &tmask = sp.tmask;
     if (!st && p->layout == LBM_SPARSE_TILE16 && pl.ntiles > 0) {
-        tmask.resize((size_t)pl.ntiles * TILE_N);
-        build_tile_masks(*p, c->mask.data(), txy.data(), pl.ntiles, tmask.data());
         // device neighbour table in 3x3 order: [t][3*(oy+1) + (ox+1)]
         nbr3.resize((size_t)pl.ntiles * 9);
         for (int t = 0; t < pl.ntiles; ++t)
@@ -330,9 +365,20 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
         if (!st)
             st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_tid, c->tile_id.data(), c->tile_id.size() * 4,
                                                cudaMemcpyHostToDevice, s), "copy tile ids");
+        if (!st && pl.use_list && !sp.list2.empty())
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_list2, sp.list2.data(), sp.list2.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy vector list");
+        if (!st && pl.use_list && !sp.list4.empty())
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_list4, sp.list4.data(), sp.list4.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy vector list");
         g.nbr = reinterpret_cast<const int32_t *>(ws + pl.off_nbr);
         g.tile_xy = reinterpret_cast<const int32_t *>(ws + pl.off_txy);
         g.tile_id = reinterpret_cast<const int32_t *>(ws + pl.off_tid);
+        g.use_list = pl.use_list;
+        g.nlist2 = (int)sp.list2.size();
+        g.nlist4 = (int)sp.list4.size();
+        g.vlist2 = reinterpret_cast<const unsigned *>(ws + pl.off_list2);
+        g.vlist4 = reinterpret_cast<const unsigned *>(ws + pl.off_list4);
     } else if (p->layout == LBM_SPARSE_TILE16) {
         g.tile_id = reinterpret_cast<const int32_t *>(ws + pl.off_tid);
         if (!st)
@@ -575,8 +621,9 @@ lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id
     if (check_params(p)) return LBM_ERR_INVALID;
     std::vector<uint8_t> mask;
     std::vector<int32_t> tid, nbr, txy;
+    SparseTables sp;
     Plan pl;
-    make_plan(*p, mask, tid, nbr, txy, pl);
+    make_plan(*p, mask, tid, nbr, txy, sp, pl);
     if (h_mask) std::memcpy(h_mask, mask.data(), mask.size());
     if (p->layout == LBM_SPARSE_TILE16) {
         if (h_tile_id) std::memcpy(h_tile_id, tid.data(), tid.size() * 4);

@@ -48,6 +48,11 @@ struct Geo {
     const int32_t *tile_id;// sparse [nty][ntx]
     int has_mask;          // 0: every node fluid, both axes periodic
     int frame_y;           // dense, > 2^21 nodes, bounced links only in rows 0 and ny-1
+    // sparse: vectors of 2 / 4 nodes that hold a fluid node, as t * TPT +
+    // position in the tile (TPT = 256 / vector size), in tile order
+    int use_list;
+    int nlist2, nlist4;
+    const unsigned *vlist2, *vlist4;
 };
 
 // Physics as the kernels see it.

@@ -253,10 +253,15 @@ template <int VEC> struct DenseAddr {
 
 // Tiled sparse f[tile][slot][16][16]; thread = VEC nodes of one tile row.
 // nbr3 is the device table [tile][3*(oy+1) + (ox+1)] (absent -> -1).
-template <int VEC> struct TileAddr {
+// LIST: thread k takes the k-th entry of the list of vectors that hold a
+// fluid node (t * TPT + position in the tile), so that no warp idles on the
+// solid part of a kept tile; without it, thread k takes position k % TPT of
+// tile k / TPT.
+template <int VEC, bool LIST = false> struct TileAddr {
     enum { VEC_ = VEC, TPR = TILE / VEC, TPT = TILE * (TILE / VEC) };
     int t, lx0, ly, xv, tx, ty, nx, ny;
     bool valid;
+    bool lnb, rnb; // LIST: the lane below / above holds the vector just left / right
     const uint8_t *mask;
     // element index (slot 0) of this thread's first node in rows ly-1, ly,
     // ly+1 (rowb), and of the nodes just left (lb) and right (rb) of the
@@ -264,16 +269,31 @@ template <int VEC> struct TileAddr {
     // 9 * 256 * tiles < 2^32 is checked at create)
     unsigned rowb[3], lb[3], rb[3];
 
-    // 1-D launch over tiles (TPT threads per tile); the row argument is unused
+    // 1-D launch over tiles (TPT threads per tile) or over the list; the row
+    // argument is unused
     __device__ __forceinline__ TileAddr(const Geo &g, int gtid, int) {
         nx = g.nx;
         ny = g.ny;
         mask = g.mask;
-        int tt = gtid / TPT;
-        valid = tt < g.ntiles;
-        if (!valid) tt = g.ntiles - 1;
-        t = tt;
-        const int tl = gtid - (gtid / TPT) * TPT;
+        int tl;
+        if constexpr (LIST) {
+            const unsigned *lst = VEC == 4 ? g.vlist4 : g.vlist2;
+            const int n = VEC == 4 ? g.nlist4 : g.nlist2;
+            valid = gtid < n;
+            const unsigned e = __ldg(lst + (valid ? gtid : n - 1));
+            t = (int)(e / TPT);
+            tl = (int)(e - (unsigned)t * TPT);
+            const unsigned ep = __shfl_up_sync(LBM_FULL, e, 1), en = __shfl_down_sync(LBM_FULL, e, 1);
+            const int lane = threadIdx.x & 31;
+            lnb = lane > 0 && ep + 1u == e && (tl % TPR) > 0;
+            rnb = lane < 31 && en == e + 1u && (tl % TPR) < TPR - 1;
+        } else {
+            int tt = gtid / TPT;
+            valid = tt < g.ntiles;
+            if (!valid) tt = g.ntiles - 1;
+            t = tt;
+            tl = gtid - (gtid / TPT) * TPT;
+        }
         ly = tl / TPR;
         xv = tl - ly * TPR;
         lx0 = xv * VEC;
@@ -308,8 +328,8 @@ template <int VEC> struct TileAddr {
         if (k + dx >= VEC) return rb[dy + 1] + (unsigned)(slot * TILE_N);
         return rowb[dy + 1] + (unsigned)(slot * TILE_N + k + dx);
     }
-    __device__ __forceinline__ bool left_in_warp(int) const { return xv > 0; }
-    __device__ __forceinline__ bool right_in_warp(int) const { return xv < TPR - 1; }
+    __device__ __forceinline__ bool left_in_warp(int) const { return LIST ? lnb : xv > 0; }
+    __device__ __forceinline__ bool right_in_warp(int) const { return LIST ? rnb : xv < TPR - 1; }
     __device__ __forceinline__ int gx(int k) const { return tx * TILE + lx0 + k; }
     __device__ __forceinline__ int gy() const { return ty * TILE + ly; }
     __device__ __forceinline__ bool in_domain() const { return gy() < ny; }
@@ -1345,7 +1365,7 @@ template <int VEC> static Shape step_shape(const Geo &g) {
         sh.gx = (unsigned)((nvx + sh.bx - 1) / sh.bx);
         sh.rows = (unsigned)g.ny;
     } else {
-        const long long n = (long long)g.ntiles * TileAddr<VEC>::TPT;
+        const long long n = g.use_list ? (VEC == 4 ? g.nlist4 : g.nlist2) : (long long)g.ntiles * TileAddr<VEC>::TPT;
         sh.bx = STEP_BLOCK;
         sh.gx = (unsigned)((n + STEP_BLOCK - 1) / STEP_BLOCK);
         sh.rows = 1;
@@ -1373,15 +1393,24 @@ static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, vo
 }
 // Dense (TILED false) or tiled addressing with the vector width of the step
 // kind, the force mode and the mask flag.
-template <int P, bool TILED, int MODE, bool HM, int F>
-static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
-                            cudaStream_t s) {
-    constexpr int V = StepVec<P, HM, MODE, F>::value;
-    typedef typename std::conditional<TILED, TileAddr<V>, DenseAddr<V>>::type A;
+template <int P, class A, int MODE, bool HM, int F>
+static cudaError_t step_open(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
+                             cudaStream_t s) {
     // open sides are only on masked kernels (their links are marked)
     if constexpr (HM)
         if (ph.has_open) return step_launch<P, A, MODE, HM, F, true>(g, ph, src, dst, t, r, s);
     return step_launch<P, A, MODE, HM, F, false>(g, ph, src, dst, t, r, s);
+}
+template <int P, bool TILED, int MODE, bool HM, int F>
+static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
+                            cudaStream_t s) {
+    constexpr int V = StepVec<P, HM, MODE, F>::value;
+    if constexpr (TILED) {
+        if (g.use_list) return step_open<P, TileAddr<V, true>, MODE, HM, F>(g, ph, src, dst, t, r, s);
+        return step_open<P, TileAddr<V, false>, MODE, HM, F>(g, ph, src, dst, t, r, s);
+    } else {
+        return step_open<P, DenseAddr<V>, MODE, HM, F>(g, ph, src, dst, t, r, s);
+    }
 }
 template <int P, bool TILED, int MODE, bool HM>
 static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
