@@ -163,7 +163,7 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
     // the list pays off when a good part of the kept tiles' vectors is solid
     // (measured on 4096^2 disc media: +10-33% at 42% active vectors, -3% at 87%)
     pl.use_list = p.layout == LBM_SPARSE_TILE16 && pl.ntiles > 0 &&
-                  (double)sp.list4.size() < 0.85 * (double)pl.ntiles * (TILE_N / 4);
+                  (double)sp.list2.size() < 0.85 * (double)pl.ntiles * (TILE_N / 2);
     pl.off_list2 = off;
     if (pl.use_list) off += align256(sp.list2.size() * 4);
     pl.off_list4 = off;

@@ -1406,7 +1406,10 @@ static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void 
                             cudaStream_t s) {
     constexpr int V = StepVec<P, HM, MODE, F>::value;
     if constexpr (TILED) {
-        if (g.use_list) return step_open<P, TileAddr<V, true>, MODE, HM, F>(g, ph, src, dst, t, r, s);
+        // over the list, FP32 keeps 8-byte vectors with the bounce-back
+        // preload in every step kind (finer vectors skip more solid nodes)
+        constexpr int VL = P == LBM_F32 ? 2 : V;
+        if (g.use_list) return step_open<P, TileAddr<VL, true>, MODE, HM, F>(g, ph, src, dst, t, r, s);
         return step_open<P, TileAddr<V, false>, MODE, HM, F>(g, ph, src, dst, t, r, s);
     } else {
         return step_open<P, DenseAddr<V>, MODE, HM, F>(g, ph, src, dst, t, r, s);
