@@ -97,3 +97,45 @@ def test_porous_full_size_one_step_matches_oracle(L, orc, phi, pattern):
     w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None]
     err = np.linalg.norm(B[:, fl] - ref[:, fl]) / np.linalg.norm(ref[:, fl] - w)
     assert err <= 1e-5, err
+
+
+def test_maximum_size_sampled_nodes_match_oracle(L, orc):
+    """The largest grid the 32-bit element indices allow (9 nx ny < 2^32:
+    21760 x 21920, 477M nodes, 34 GB of FP32 lattices), periodic, smooth
+    seeded field: one GPU step against the oracle at sampled nodes, each
+    recomputed by the oracle on a 3 x 3 periodic patch cut from the GPU's
+    state around it (the node's update depends on nothing else), and mass
+    conserved over the step."""
+    nx, ny = 21760, 21920
+    assert 9 * nx * ny < 2 ** 32 <= 9 * nx * (ny + 16)
+    sim = L.LBM(nx, ny, 0.8, precision="f32")
+    y = torch.arange(ny, dtype=torch.float32, device="cuda")[:, None]
+    x = torch.arange(nx, dtype=torch.float32, device="cuda")[None, :]
+    kx, ky = 2 * np.pi / nx, 2 * np.pi / ny
+    u = torch.stack([-0.05 * torch.cos(kx * x) * torch.sin(ky * y), 0.05 * torch.sin(kx * x) * torch.cos(ky * y)])
+    rho = 1.0 + 0.01 * torch.cos(kx * x) * torch.cos(ky * y)
+    sim.init_equilibrium(rho, u)
+    del u, rho
+    m0, _ = sim.reduce()
+    A = sim.get_f()
+    sim.step(1)
+    m1, _ = sim.reduce()
+    B = sim.get_f()
+    assert abs(m1 - m0) <= 1e-9 * m0
+    rng = inputs.SplitMix64(inputs.FD_SEED)
+    pts = [(0, 0), (ny - 1, nx - 1), (ny // 2, nx // 3)]
+    pts += [(int(rng.next_u64() % ny), int(rng.next_u64() % nx)) for _ in range(29)]
+    s = orc.Setup(nx=3, ny=3, tau=0.8)
+    mask, _ = orc.link_mask(s)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    for (py, px) in pts:
+        ys = torch.tensor([(py - 1) % ny, py, (py + 1) % ny], device="cuda")
+        xs = torch.tensor([(px - 1) % nx, px, (px + 1) % nx], device="cuda")
+        patch = A[:, ys][:, :, xs].double().cpu().numpy()
+        ref = orc.step(s, mask, patch)[:, 1, 1]
+        got = B[:, py, px].double().cpu().numpy()
+        err = np.abs(got - ref).max() / np.abs(ref - w).max()
+        assert err <= 1e-5, ((py, px), err)
+    del A, B
+    sim.close()
+    torch.cuda.empty_cache()

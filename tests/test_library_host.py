@@ -33,6 +33,7 @@ def test_status_strings(lbm):
 @pytest.mark.parametrize("bad", [
     dict(nx=24), dict(nx=0), dict(ny=0), dict(tau=0.5), dict(tau=float("nan")),
     dict(periodic_mismatch=True), dict(sparse_periodic_ny=True),
+    dict(nx=21760, ny=21936),  # 9 nx ny >= 2^32: beyond 32-bit element indices
 ])
 def test_invalid_parameters_rejected(lbm, bad):
     nx, ny, tau = bad.get("nx", 32), bad.get("ny", 16), bad.get("tau", 0.8)
