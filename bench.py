@@ -172,6 +172,16 @@ def build_case(workload: str, n: int, precision: str):
     raise ValueError(workload)
 
 
+def sector_nodes(solid: np.ndarray, precision: str) -> int:
+    """Nodes in the 32-byte DRAM sectors (aligned runs of 32 / s nodes along
+    x) that hold a fluid node: the bytes any step must move at sector
+    granularity on this geometry are 2 q s per such node."""
+    seg = 32 // BYTES_PER_VALUE[precision]
+    ny, nx = solid.shape
+    fl = (solid == 0)[:, : nx // seg * seg].reshape(ny, nx // seg, seg)
+    return int(fl.any(axis=2).sum()) * seg
+
+
 def max_over_ranks(value: float, dist, device) -> float:
     """The largest value over all ranks (every rank gets it)."""
     if dist is None:
@@ -450,10 +460,11 @@ def extra_measurements(args):
             key = "porous_phi%.2f_%d/%s/%s/%s" % (achieved, n, prec, layout, pattern)
             g = record(key, nf, k, t, prec)
             if kept["nodes"]:
-                # the tiled layout's own bound: every node of a kept tile moves
                 out[key]["kept_tile_nodes"] = kept["nodes"]
-                out[key]["frac_of_layout_roofline"] = round(
-                    g * kept["nodes"] / nf * node_bytes(prec) / peak, 4)
+            # the geometry's own bound at DRAM sector granularity
+            sec = sector_nodes(solid, prec)
+            out[key]["sector_nodes"] = sec
+            out[key]["frac_of_sector_roofline"] = round(g * sec / nf * node_bytes(prec) / peak, 4)
             if layout == "sparse" and (prec, layout, pattern) in dense_geom:
                 out["porous_phi%.2f_%d/%s/%s/%s" % (achieved, n, prec, layout, pattern)]["eta_P"] = round(
                     g / dense_geom[(prec, layout, pattern)], 3)
@@ -507,8 +518,8 @@ def porosity_sweep(n: int = 4096, steps: int = 300):
                             "frac_of_measured_hbm": round(g * node_bytes("f32") / peak, 4)}
                 if tiles is not None:
                     row["kept_tiles"] = int(tiles)
-                    row[lay]["frac_of_layout_roofline"] = round(
-                        g * tiles * 256 / nf * node_bytes("f32") / peak, 4)
+                row[lay]["frac_of_sector_roofline"] = round(
+                    g * sector_nodes(solid, "f32") / nf * node_bytes("f32") / peak, 4)
             row["fluid_nodes"] = int(nf)
             rows.append(row)
         res[name] = rows

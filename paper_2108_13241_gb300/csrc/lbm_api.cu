@@ -375,6 +375,7 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
         g.tile_xy = reinterpret_cast<const int32_t *>(ws + pl.off_txy);
         g.tile_id = reinterpret_cast<const int32_t *>(ws + pl.off_tid);
         g.use_list = pl.use_list;
+        g.active_frac = (float)((double)sp.list2.size() / ((double)pl.ntiles * (TILE_N / 2)));
         g.nlist2 = (int)sp.list2.size();
         g.nlist4 = (int)sp.list4.size();
         g.vlist2 = reinterpret_cast<const unsigned *>(ws + pl.off_list2);

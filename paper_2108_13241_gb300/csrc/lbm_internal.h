@@ -4,7 +4,6 @@
 
 #include <cstddef>
 #include <cstdint>
-#include <vector>
 #include <cuda_runtime.h>
 
 #include "lbm.h"
@@ -51,6 +50,7 @@ struct Geo {
     // sparse: vectors of 2 / 4 nodes that hold a fluid node, as t * TPT +
     // position in the tile (TPT = 256 / vector size), in tile order
     int use_list;
+    float active_frac;     // listed 2-node vectors / all vectors of kept tiles
     int nlist2, nlist4;
     const unsigned *vlist2, *vlist4;
 };

@@ -201,7 +201,7 @@ __device__ __forceinline__ int pick3(int o, int a, int b, int c) { return o < 0 
 
 // Dense SoA f[slot][ny][nx]; thread = VEC nodes (x0..x0+VEC-1, y).
 template <int VEC> struct DenseAddr {
-    enum { VEC_ = VEC };
+    enum { VEC_ = VEC, LIST_ = 0 };
     int x0, y, xv, nvx, nx, ny;
     bool valid;
     unsigned nslot; // element indices fit 32 bits (checked at create)
@@ -258,7 +258,7 @@ template <int VEC> struct DenseAddr {
 // solid part of a kept tile; without it, thread k takes position k % TPT of
 // tile k / TPT.
 template <int VEC, bool LIST = false> struct TileAddr {
-    enum { VEC_ = VEC, TPR = TILE / VEC, TPT = TILE * (TILE / VEC) };
+    enum { VEC_ = VEC, LIST_ = LIST, TPR = TILE / VEC, TPT = TILE * (TILE / VEC) };
     int t, lx0, ly, xv, tx, ty, nx, ny;
     bool valid;
     bool lnb, rnb; // LIST: the lane below / above holds the vector just left / right
@@ -1355,7 +1355,7 @@ struct Shape {
     unsigned bx, gx, rows;
     bool dense;
 };
-template <int VEC> static Shape step_shape(const Geo &g) {
+template <int VEC, bool LIST = false> static Shape step_shape(const Geo &g) {
     Shape sh;
     sh.dense = g.layout == LBM_DENSE;
     if (sh.dense) {
@@ -1365,7 +1365,7 @@ template <int VEC> static Shape step_shape(const Geo &g) {
         sh.gx = (unsigned)((nvx + sh.bx - 1) / sh.bx);
         sh.rows = (unsigned)g.ny;
     } else {
-        const long long n = g.use_list ? (VEC == 4 ? g.nlist4 : g.nlist2) : (long long)g.ntiles * TileAddr<VEC>::TPT;
+        const long long n = LIST ? (VEC == 4 ? g.nlist4 : g.nlist2) : (long long)g.ntiles * TileAddr<VEC>::TPT;
         sh.bx = STEP_BLOCK;
         sh.gx = (unsigned)((n + STEP_BLOCK - 1) / STEP_BLOCK);
         sh.rows = 1;
@@ -1381,7 +1381,7 @@ struct Rows {
 template <int P, class A, int MODE, bool HM, int F, bool OPEN>
 static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                                cudaStream_t s) {
-    const Shape sh = step_shape<A::VEC_>(g);
+    const Shape sh = step_shape<A::VEC_, A::LIST_>(g);
     if (sh.gx == 0) return cudaSuccess;
     const unsigned rows = sh.dense ? (unsigned)r.nrows : 1u;
     for (unsigned k = 0; k < rows; k += 65535u) {
@@ -1407,9 +1407,13 @@ static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void 
     constexpr int V = StepVec<P, HM, MODE, F>::value;
     if constexpr (TILED) {
         // over the list, FP32 keeps 8-byte vectors with the bounce-back
-        // preload in every step kind (finer vectors skip more solid nodes)
+        // preload in every step kind (finer vectors skip more solid nodes);
+        // the FP32 two-lattice step without it moves 16-byte vectors, which
+        // wins until about a third of the vectors are solid
         constexpr int VL = P == LBM_F32 ? 2 : V;
-        if (g.use_list) return step_open<P, TileAddr<VL, true>, MODE, HM, F>(g, ph, src, dst, t, r, s);
+        constexpr bool WIDE = P == LBM_F32 && MODE == MODE_TWO_LATTICE && F != FORCE_FIELD;
+        if (g.use_list && g.active_frac < (WIDE ? 0.67f : 0.85f))
+            return step_open<P, TileAddr<VL, true>, MODE, HM, F>(g, ph, src, dst, t, r, s);
         return step_open<P, TileAddr<V, false>, MODE, HM, F>(g, ph, src, dst, t, r, s);
     } else {
         return step_open<P, DenseAddr<V>, MODE, HM, F>(g, ph, src, dst, t, r, s);

@@ -293,3 +293,45 @@ def test_wall_rows_low_precision(L, orc, precision, tol):
         g = run_gpu(L, case, 300, precision, layout, pattern)
         err = C.rel_l2(g["u"], o["u"])
         assert err <= tol, (layout, pattern, err)
+
+
+def _active_vector_fraction(solid):
+    """2-node vectors along tile rows that hold a fluid node, over all
+    vectors of the 16x16 tiles that hold one (the tiled step switches to its
+    vector list below 0.67 / 0.85 of this)."""
+    ny, nx = solid.shape
+    pad = np.ones(((ny + 15) // 16 * 16, nx), np.uint8)
+    pad[:ny] = solid
+    fl = pad == 0
+    tiles = fl.reshape(fl.shape[0] // 16, 16, nx // 16, 16).any(axis=(1, 3))
+    return fl.reshape(fl.shape[0], nx // 2, 2).any(axis=2).sum() / (tiles.sum() * 128)
+
+
+@pytest.mark.parametrize("layout,pattern", VARIANTS)
+@pytest.mark.parametrize("steps", [1, 2, 33])
+def test_low_porosity_vector_list_fp64_matches_oracle(L, orc, layout, pattern, steps):
+    """Discs r in [4, 10] at porosity 0.3 on 256 x 200 (ragged last tile
+    row): under half of the kept tiles' vectors hold fluid, so the tiled
+    step runs over its vector list in every step kind."""
+    case = C.discs(256, 200, 0.3, seed=inputs.GEOMETRY_SEED + 5, rmin=4.0, rmax=10.0)
+    assert _active_vector_fraction(case.solid) < 0.6
+    case.rho0 = 1.0 + 0.01 * inputs.random_field((case.ny, case.nx), 811)
+    case.u0 = 0.02 * inputs.random_field((2, case.ny, case.nx), 812)
+    o = oracle_cached(orc, case, steps)
+    g = run_gpu(L, case, steps, "f64", layout, pattern)
+    fl = o["mask"] != 0xFF
+    assert C.rel_l2(g["f"], o["f"], fl) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32", "f16s"])
+def test_low_porosity_vector_list_bitwise_equals_dense(L, precision):
+    case = C.discs(256, 200, 0.3, seed=inputs.GEOMETRY_SEED + 5, rmin=4.0, rmax=10.0)
+    case.rho0 = 1.0 + 0.01 * inputs.random_field((case.ny, case.nx), 811)
+    case.u0 = 0.02 * inputs.random_field((2, case.ny, case.nx), 812)
+    ref = None
+    for layout, pattern in VARIANTS:
+        g = run_gpu(L, case, 9, precision, layout, pattern)
+        if ref is None:
+            ref = g["f"]
+        else:
+            assert np.array_equal(g["f"], ref), (precision, layout, pattern)
