@@ -13,12 +13,14 @@
 //    lane (__shfl_up/down_sync); only lanes at a warp or row edge load that
 //    value from memory (an L1/L2 hit);
 //  * a per-node link mask (one byte) selects a divergent slow path only at
-//    nodes next to walls or obstacles; all-solid vectors move no data;
+//    nodes next to walls, open sides or obstacles; all-solid vectors move no
+//    data; on porous tiled geometries threads run only over the vectors that
+//    hold fluid (a host-built list);
 //  * distributions are stored shifted, f_i - w_i, and the collision runs in
 //    shifted variables (rho = 1 + sum, m = sum c_i (f_i - w_i)), so FP32 and
 //    FP16 keep their mantissa for the small deviations from rest;
-//  * every variant (dense / tiled, two-lattice / AA) feeds the same
-//    `collide` with the same operands, so FP64 variants agree bit for bit.
+//  * every variant (dense / tiled / listed, two-lattice / AA) feeds the same
+//    `collide` with the same operands, so results agree bit for bit.
 #pragma once
 #include <type_traits>
 
