@@ -561,15 +561,14 @@ def channel_runs(steps: int = 1_000_000):
     return {"sweep": "channels", "results": out}
 
 
-def adjoint_cost():
+def adjoint_cost(nx=512, ny=256, T=2000, K=45, count=12, rmin=6, rmax=12):
     """Cost of one adjoint step relative to one forward step on the
-    differentiable channel (512 x 256, 12 cylinders, FP32, T = 2000,
-    checkpoint every 45): backward wall time (recompute + adjoint) / T over
-    plain forward step time."""
+    differentiable channel (default: 512 x 256, 12 cylinders, FP32,
+    T = 2000, checkpoint every 45): backward wall time (recompute + adjoint)
+    / T over plain forward step time."""
     import torch
     from paper_2108_13241_gb300 import autograd as ag, inputs, lbm
-    nx, ny, T, K = 512, 256, 2000, 45
-    solid, _ = inputs.channel_cylinders(nx, ny, count=12, rmin=6, rmax=12, clearance=2)
+    solid, _ = inputs.channel_cylinders(nx, ny, count=count, rmin=rmin, rmax=rmax, clearance=2)
     F = np.zeros((2, ny, nx), np.float32)
     F[0] = 1e-5
     ut = torch.as_tensor(inputs.target_velocity(nx, ny, solid), dtype=torch.float32, device="cuda")
@@ -593,10 +592,15 @@ def adjoint_cost():
         ev[2].synchronize()
     t_fwd = ev[0].elapsed_time(ev[1]) / 1e3
     t_bwd = ev[1].elapsed_time(ev[2]) / 1e3
+    nf = int((solid == 0).sum())
+    # the adjoint kernel's share of a backward step: one recompute step is
+    # the rest; algorithmic bytes of k_adjoint: 33 FP32 values per node
+    t_adj = max(t_bwd / T - t_step, 1e-12)
     return {"forward_step_us": round(t_step * 1e6, 2),
             "checkpointed_forward_step_us": round(t_fwd / T * 1e6, 2),
             "backward_step_us": round(t_bwd / T * 1e6, 2),
             "adjoint_over_forward": round(t_bwd / T / t_step, 3),
+            "adjoint_kernel_GBps_algorithmic": round(nf * 33 * 4 / t_adj / 1e9, 1),
             "grad_finite": bool(torch.isfinite(Fg.grad).all().item())}
 
 
@@ -685,12 +689,23 @@ def main():
                     help="run the 4096^2 eta_P sweep over porosity instead of the benchmark")
     ap.add_argument("--channels", action="store_true",
                     help="run the paper's two channel flows (4096 x 512, 10^6 steps) instead of the benchmark")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="run the adjoint cost on the 512 x 256 channel and on a 2048 x 2048 one")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.sweep or args.porosity_sweep or args.channels:
+    if args.sweep or args.porosity_sweep or args.channels or args.adjoint:
         import __graft_entry__
         __graft_entry__.build()
-        res = precision_sweep() if args.sweep else (porosity_sweep() if args.porosity_sweep else channel_runs())
+        if args.sweep:
+            res = precision_sweep()
+        elif args.porosity_sweep:
+            res = porosity_sweep()
+        elif args.channels:
+            res = channel_runs()
+        else:
+            res = {"sweep": "adjoint", "results": {
+                "channel_512x256_T2000_K45": adjoint_cost(),
+                "channel_2048x2048_T40_K8": adjoint_cost(2048, 2048, 40, 8, count=96, rmin=12, rmax=24)}}
         print(json.dumps(res), flush=True)
         return 0
 

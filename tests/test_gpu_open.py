@@ -155,3 +155,20 @@ def test_open_y_sides_without_obstacles_fp64(L, orc, layout, pattern):
     o = run_oracle(orc, c, 61)
     g = run_gpu(L, c, 61, "f64", layout, pattern)
     assert C.rel_l2(g["f"], o["f"]) <= 1e-12
+
+
+@pytest.mark.parametrize("layout,pattern", VARIANTS)
+def test_open_sides_over_low_porosity_fp64(L, orc, layout, pattern):
+    """Velocity inlet and pressure outlet across a low-porosity disc medium
+    (the tiled step runs over its vector list with the open-side rule)."""
+    solid, _, _ = inputs.porous_discs(256, 160, 0.35, rmin=4, rmax=10, seed=inputs.GEOMETRY_SEED + 9)
+    solid[:, :2] = 0
+    solid[:, -2:] = 0
+    c = C.Case("openporous", 256, 160, 0.75, px=False, py=False, solid=solid,
+               open={"west": ("velocity", (0.02, 0.0)), "east": ("pressure", 1.0)})
+    c.rho0 = 1.0 + 0.005 * inputs.random_field((160, 256), 901)
+    c.u0 = 0.01 * inputs.random_field((2, 160, 256), 902)
+    o = run_oracle(orc, c, 45)
+    g = run_gpu(L, c, 45, "f64", layout, pattern)
+    fl = o["mask"] != 0xFF
+    assert C.rel_l2(g["f"], o["f"], fl) <= 1e-12
