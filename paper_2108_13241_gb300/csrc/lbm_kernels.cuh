@@ -455,8 +455,10 @@ template <class C> struct Coef {
 // is formed error-free, because a constant rounded to FP32 would scale the
 // equilibrium momentum of every node by the same (1 + eps) each step -- a
 // bias that grows linearly with the step count in slowly varying flows.
-// FP16s storage rounding (2^-21 relative to w_i) dwarfs that bias, so its
-// kernels keep the cheaper form 3 omega w_i rho (c_i . u).
+// FP16s (on its 2^10 scale) applies the float pair without the error-free
+// product: that removes the bias of the rounded constant, the same for every
+// node and step; what the product's rounding leaves varies from node to
+// node and is far below binary16's storage rounding.
 // SC: f in units of SC (the FP16s step works in f - w times 2^10, so its
 // decode and encode need no scaling); the constants that multiply plain
 // quantities (rho, u, F) carry the factor.
@@ -498,7 +500,8 @@ __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
         } else if constexpr (sizeof(C) == 8) {                                              \
             qh = co.kh[Q] * (SH);                                                           \
         } else {                                                                            \
-            qh = (C(3) * RQ) * t;                                                           \
+            qh = co.kh[Q] * (SH);                                                           \
+            ql = co.kl[Q] * (SH);                                                           \
         }                                                                                   \
         if (HAS_F) {                                                                        \
             const C cf = (CF);                                                              \
