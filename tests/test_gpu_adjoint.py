@@ -159,3 +159,14 @@ def test_force_gradient_matches_fp64_finite_differences_full_size(L):
         norm_err, np.max(np.abs(a32 - fd) / np.maximum(np.abs(fd), floor))))
     assert norm_err <= 1e-4, norm_err
     assert np.max(np.abs(a32 - fd) / np.maximum(np.abs(fd), floor)) <= 5e-4
+
+
+@pytest.mark.parametrize("layout,pattern", [("sparse", "two_lattice"), ("dense", "aa")])
+def test_adjoint_refuses_unsupported_configurations(L, layout, pattern):
+    lbm, _ = L
+    c = channel_case()
+    sim = lbm.LBM(precision="f64", layout=layout, pattern=pattern, **C.gpu_kwargs(c))
+    lam = torch.zeros((9, c.ny, c.nx), dtype=torch.float64, device="cuda")
+    with pytest.raises(lbm.LBMError) as e:
+        sim.macros_backward(None, torch.zeros((2, c.ny, c.nx), dtype=torch.float64, device="cuda"), lam, None)
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
