@@ -7,8 +7,9 @@
  * BGK operator (Eq. 4, Eq. 5, Eq. 6), the moments of
  * Eq. 2, half-way bounce-back walls and obstacles (Sec. 3, boundary
  * paragraph), dense and 16x16-tiled sparse storage (Sec. 4.2.2, "tile" and
- * "pointer tile" layouts), plus a Guo body force, an in-place AA pattern,
- * FP64 / FP32 / FP16-shifted storage and a hand-written adjoint.
+ * "pointer tile" layouts), the constant-velocity and constant-pressure
+ * open sides of Sec. 3 (after Zou & He), plus a Guo body force, an in-place
+ * AA pattern, FP64 / FP32 / FP16-shifted storage and a hand-written adjoint.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
