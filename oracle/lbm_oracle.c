@@ -23,7 +23,8 @@
  *                        after Zou & He 1997), in the gather of the step
  *                        and the macros (orc_open_side, step_body.inc);
  *   orc_adjoint_step     discrete adjoint (transpose of the linearisation) of
- *                        orc_step;
+ *                        orc_step, open sides included (their rules are
+ *                        affine in f', orc_open_transpose);
  *   orc_macros_adjoint   transpose of orc_macros.
  * Pins: tests/test_oracle_*.py (closed forms, invariants, Poiseuille,
  * Taylor-Green decay, brute-force tables, dot-product and complex-step checks).
@@ -188,9 +189,27 @@ static int orc_has_open(const orc_params *p)
     return 0;
 }
 
-static void orc_fill_nan(double *a, long n)
+/* Transpose of the open-side rules at node (x, y), applied to g: the rules
+ * are affine in the gathered f' (orc_open_side), so their linear part is
+ * M[:, j] = R(e_j) - R(0); g becomes M^T g.  Identity away from open sides. */
+static void orc_open_transpose(const orc_params *p, int x, int y, double g[9])
 {
-    for (long k = 0; k < n; ++k) a[k] = NAN;
+    double r0[9] = {0}, M[9][9];
+    for (int s = 0; s < 4; ++s)
+        if (p->open_kind[s] != ORC_OPEN_NONE) orc_open_side(p, s, x, y, r0);
+    for (int j = 0; j < 9; ++j) {
+        double e[9] = {0};
+        e[j] = 1.0;
+        for (int s = 0; s < 4; ++s)
+            if (p->open_kind[s] != ORC_OPEN_NONE) orc_open_side(p, s, x, y, e);
+        for (int i = 0; i < 9; ++i) M[i][j] = e[i] - r0[i];
+    }
+    double out[9];
+    for (int j = 0; j < 9; ++j) {
+        out[j] = 0.0;
+        for (int i = 0; i < 9; ++i) out[j] += M[i][j] * g[i];
+    }
+    for (int j = 0; j < 9; ++j) g[j] = out[j];
 }
 
 /* Shared by the macros and the adjoints: the gather of step 1 at node (x, y),
@@ -273,7 +292,7 @@ void orc_adjoint_step(const orc_params *p, const uint8_t *mask,
     const long N = (long)p->nx * p->ny;
     const double omega = 1.0 / p->tau;
     const double k = 1.0 - 0.5 * omega;
-    if (orc_has_open(p)) { orc_fill_nan(lam, 9 * N); return; }
+    const int open = orc_has_open(p);
     memset(lam, 0, sizeof(double) * 9 * N);
     for (int y = 0; y < p->ny; ++y) {
         for (int x = 0; x < p->nx; ++x) {
@@ -283,6 +302,8 @@ void orc_adjoint_step(const orc_params *p, const uint8_t *mask,
             int bounced[9];
             long src[9];
             orc_gather(p, mask, A, x, y, f, bounced, src);
+            for (int s = 0; s < 4; ++s)
+                if (p->open_kind[s] != ORC_OPEN_NONE) orc_open_side(p, s, x, y, f);
             double rho = 0, mx = 0, my = 0;
             for (int i = 0; i < 9; ++i) {
                 rho += f[i];
@@ -310,14 +331,17 @@ void orc_adjoint_step(const orc_params *p, const uint8_t *mask,
                 gFx += li * k * W[i] * (3.0 * (CX[i] - ux) + 9.0 * cu * CX[i]);
                 gFy += li * k * W[i] * (3.0 * (CY[i] - uy) + 9.0 * cu * CY[i]);
             }
+            double g[9];
             for (int j = 0; j < 9; ++j) {
                 const double lj = lam_next[j * N + n];
-                const double g = (1.0 - omega) * lj + a +
-                                 ((CX[j] - ux) * Vx + (CY[j] - uy) * Vy) / rho;
+                g[j] = (1.0 - omega) * lj + a + ((CX[j] - ux) * Vx + (CY[j] - uy) * Vy) / rho;
+            }
+            if (open) orc_open_transpose(p, x, y, g);
+            for (int j = 0; j < 9; ++j) {
                 if (!bounced[j])
-                    lam[j * N + src[j]] += g;
+                    lam[j * N + src[j]] += g[j];
                 else
-                    lam[OPP[j] * N + n] += g;
+                    lam[OPP[j] * N + n] += g[j];
             }
             if (grad_force) {
                 const long gn = force ? n : 0;
@@ -341,7 +365,7 @@ void orc_macros_adjoint(const orc_params *p, const uint8_t *mask,
                         const double *g_uy, double *lam, double *grad_force)
 {
     const long N = (long)p->nx * p->ny;
-    if (orc_has_open(p)) { orc_fill_nan(lam, 9 * N); return; }
+    const int open = orc_has_open(p);
     for (int y = 0; y < p->ny; ++y) {
         for (int x = 0; x < p->nx; ++x) {
             const long n = (long)y * p->nx + x;
@@ -350,6 +374,8 @@ void orc_macros_adjoint(const orc_params *p, const uint8_t *mask,
             int bounced[9];
             long src[9];
             orc_gather(p, mask, A, x, y, f, bounced, src);
+            for (int s = 0; s < 4; ++s)
+                if (p->open_kind[s] != ORC_OPEN_NONE) orc_open_side(p, s, x, y, f);
             double rho = 0, mx = 0, my = 0;
             for (int i = 0; i < 9; ++i) {
                 rho += f[i];
@@ -363,12 +389,14 @@ void orc_macros_adjoint(const orc_params *p, const uint8_t *mask,
             const double gr = g_rho ? g_rho[n] : 0.0;
             const double gx = g_ux ? g_ux[n] : 0.0;
             const double gy = g_uy ? g_uy[n] : 0.0;
+            double g[9];
+            for (int j = 0; j < 9; ++j) g[j] = gr + ((CX[j] - ux) * gx + (CY[j] - uy) * gy) / rho;
+            if (open) orc_open_transpose(p, x, y, g);
             for (int j = 0; j < 9; ++j) {
-                const double g = gr + ((CX[j] - ux) * gx + (CY[j] - uy) * gy) / rho;
                 if (!bounced[j])
-                    lam[j * N + src[j]] += g;
+                    lam[j * N + src[j]] += g[j];
                 else
-                    lam[OPP[j] * N + n] += g;
+                    lam[OPP[j] * N + n] += g[j];
             }
             if (grad_force) {
                 const long gn = force ? n : 0;

@@ -64,8 +64,6 @@ void orc_run(const orc_params *p, const uint8_t *mask, const double *force,
              double *A, double *B, int nsteps);
 void orc_macros(const orc_params *p, const uint8_t *mask, const double *force,
                 const double *A, double *rho, double *ux, double *uy);
-/* The adjoints are those of steps without open sides; with an open side
- * they write NaN to lam. */
 void orc_adjoint_step(const orc_params *p, const uint8_t *mask,
                       const double *force, const double *A,
                       const double *lam_next, double *lam, double *grad_force);

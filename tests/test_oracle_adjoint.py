@@ -15,6 +15,16 @@ CASES = {
     "periodic": (8, 8, True, True, None, 0.0, True),
     "channel": (16, 12, True, False, [(0, 0), (0, 0), (0.0, 0.0), (0.05, 0.0)], 0.15, True),
     "cavity": (12, 10, False, False, [(0, 0), (0, 0), (0, 0), (0.1, 0.0)], 0.1, False),
+    # open sides: velocity inlet (per-node profile) and pressure outlet in x
+    # with walls in y; pressure inlet and velocity outlet in y, periodic x
+    "open_x": (16, 10, False, False, [(0, 0), (0, 0), (0.02, 0.0), (0, 0)], 0.1, True),
+    "open_y": (10, 14, True, False, None, 0.1, False),
+}
+OPEN = {
+    "open_x": lambda ny, nx: {0: ("velocity", np.stack([0.03 + 0.01 * inputs.random_field((ny,), 51),
+                                                         0.005 * inputs.random_field((ny,), 52)])),
+                              1: ("pressure", 1.0 + 0.002 * inputs.random_field((ny,), 53))},
+    "open_y": lambda ny, nx: {2: ("pressure", 1.004), 3: ("velocity", (0.01, 0.02))},
 }
 
 
@@ -23,6 +33,8 @@ def _setup(orc, name):
     kw = {}
     if walls is not None:
         kw["wall_u"] = walls
+    if name in OPEN:
+        kw["open"] = OPEN[name](ny, nx)
     s = orc.Setup(nx=nx, ny=ny, tau=0.7, periodic_x=px, periodic_y=py,
                   force=(0.0, 0.0) if field else (2e-4, -1e-4), **kw)
     solid = inputs.random_solid(nx, ny, frac, seed=nx + 3 * ny) if frac else None
@@ -83,7 +95,7 @@ def _grad_through(orc, s, mask, A0, F, T, u_target):
     return lam, gF
 
 
-@pytest.mark.parametrize("name", ["periodic", "channel"])
+@pytest.mark.parametrize("name", ["periodic", "channel", "open_x"])
 def test_adjoint_matches_central_differences(orc, name):
     s, mask, F, A0 = _setup(orc, name)
     T = 12

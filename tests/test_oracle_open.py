@@ -149,10 +149,3 @@ def test_pressure_driven_channel_steady_state(orc):
     assert curv < 0 and dpdx < 0
     assert abs(nu * curv - dpdx / rho[:, xm].mean()) <= 1e-2 * abs(dpdx)
 
-
-def test_oracle_adjoint_refuses_open_sides(orc):
-    """The oracle's adjoint is that of steps without open sides; with one it
-    returns NaN rather than a wrong gradient."""
-    s, mask, A, _, _ = _channel(orc)
-    lam = orc.adjoint_step(s, mask, A, np.ones_like(A))
-    assert np.isnan(lam).all()
