@@ -94,9 +94,9 @@ typedef enum { LBM_SIDE_WALL = 0, LBM_SIDE_VELOCITY = 1, LBM_SIDE_PRESSURE = 2 }
  *   rho (1 + u . n) = sum_{c.n=0} f_j + 2 sum_{c.n>0} f_j,
  * t the tangent along the side (Zou & He 1997 for every side).  Corner links
  * that also cross a wall follow the wall.  Two adjacent sides cannot both be
- * open.  Open sides work with every precision, layout and pattern; the
- * adjoint calls (lbm_backward, lbm_macros_backward) return
- * LBM_ERR_UNSUPPORTED for them.  lbm_set_side_values gives per-node values. */
+ * open.  Open sides work with every precision, layout and pattern, and in the
+ * adjoint calls (whose rules are the transpose of these affine maps).
+ * lbm_set_side_values gives per-node values. */
 typedef struct {
     int periodic;
     double ux, uy;   /* wall velocity, or the velocity of a velocity side */

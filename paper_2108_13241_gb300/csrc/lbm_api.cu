@@ -567,7 +567,6 @@ lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n, void *
     LBM_CTX_CHECK(ctx);
     if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
         return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
-    if (ctx->phys.has_open) return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint of open sides is not available");
     if (n < 0 || (n > 0 && (!h_states || !d_lambda || !d_lambda_tmp || !d_grad_force)))
         return fail(ctx, LBM_ERR_INVALID, "bad backward arguments");
     if (((uintptr_t)d_lambda & 15) || ((uintptr_t)d_lambda_tmp & 15) || ((uintptr_t)d_grad_force & 15))
@@ -593,7 +592,6 @@ lbm_status lbm_macros_backward(lbm_ctx *ctx, const void *d_grad_rho, const void 
     LBM_CTX_CHECK(ctx);
     if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
         return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
-    if (ctx->phys.has_open) return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint of open sides is not available");
     if (!d_lambda) return fail(ctx, LBM_ERR_INVALID, "d_lambda is NULL");
     return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision,
                                         launch_macros_adjoint<P>(ctx->geo, ctx->phys, ctx->lat[ctx->cur],

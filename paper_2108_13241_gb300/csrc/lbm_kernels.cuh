@@ -953,12 +953,43 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
 
 // ------------------------------------------------------------- adjoint kernel
 
+// Transpose of the open-side rules at node (x, y) applied to g: the rules are
+// affine in the gathered f', so their linear part is M[:, j] = R(e_j) - R(0)
+// and g becomes M^T g (identity off the open sides' rows and columns).
+template <class C>
+__device__ void open_transpose(const Geo &g, const Phys &ph, int x, int y, unsigned m, C gv[9]) {
+    if (!ph.has_open || m == 0u) return;
+    if (!((x == 0 || x == g.nx - 1) && (ph.open_kind[0] || ph.open_kind[1])) &&
+        !((y == 0 || y == g.ny - 1) && (ph.open_kind[2] || ph.open_kind[3])))
+        return;
+    C r0[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) r0[i] = C(0);
+    apply_open<C>(g, ph, x, y, m, r0);
+    C out[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        C e[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) e[i] = C(i == j ? 1 : 0);
+        apply_open<C>(g, ph, x, y, m, e);
+        C acc = C(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) acc += (e[i] - r0[i]) * gv[i];
+        out[j] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) gv[j] = out[j];
+}
+
 // One adjoint step on the dense two-lattice layout: re-gathers f' from the
 // stored state A_t, reads lam_in = dL/dA_{t+1} at the node, and pushes
 // g_j = dL/df'_j back along each link (to slot j at x - c_j, or to slot
 // opp(j) at x for a bounced link): the transpose of the pull gather.  Every
-// target has one writer; solid nodes write 0 to their own slots.
-template <int P, int FORCE>
+// target has one writer; solid nodes write 0 to their own slots.  OPEN: the
+// gathered f' of nodes on an open side pass through the open-side rules, and
+// their gradients through the rules' transpose.
+template <int P, int FORCE, bool OPEN>
 __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys ph, const void *state_v,
                                                         const void *lam_in_v, void *lam_out_v, void *gF_v,
                                                         int y0) {
@@ -1017,10 +1048,12 @@ __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys 
             C f[9];                                                                       \
             node_values<S, ((K) < VEC ? (K) : 0), MODE_TWO_LATTICE>(raw, edge, f);        \
             if (m != 0u) bounce<S, MODE_TWO_LATTICE>(g, ph, ad, src, raw, own, (K), m, f);\
+            if constexpr (OPEN) apply_open<C>(g, ph, ad.gx(K), ad.gy(), m, f);           \
             C l[9], gg[9];                                                                \
             for (int j = 0; j < 9; ++j) l[j] = lam[j][(K)];                               \
             adjoint_node<C, FORCE != FORCE_NONE>(f, l, Fx[(K)], Fy[(K)], omega, gg,       \
                                                  dFx[(K)], dFy[(K)]);                     \
+            if constexpr (OPEN) open_transpose<C>(g, ph, ad.gx(K), ad.gy(), m, gg);      \
             for (int j = 0; j < 9; ++j) gout[j][(K)] = gg[j];                             \
         }                                                                                 \
     }
@@ -1327,15 +1360,20 @@ __global__ void k_macros_adjoint(const Geo g, const Phys ph, const void *state_v
     }
     C f[9];
     gather_node<S>(g, ph, PH_PLAIN, reinterpret_cast<const typename S::R *>(state_v), x, y, m, f);
+    apply_open<C>(g, ph, x, y, m, f);
     C Fx, Fy, drho, r, inv, ux, uy;
     node_force<C>(g, ph, n, Fx, Fy);
     moments<C, true>(f, Fx, Fy, drho, r, inv, ux, uy);
     const C gr = grho_v ? reinterpret_cast<const C *>(grho_v)[n] : C(0);
     const C gx = gu_v ? reinterpret_cast<const C *>(gu_v)[n] : C(0);
     const C gy = gu_v ? reinterpret_cast<const C *>(gu_v)[g.nnode + n] : C(0);
+    C gv[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) gv[j] = gr + ((C(cx(j)) - ux) * gx + (C(cy(j)) - uy) * gy) * inv;
+    open_transpose<C>(g, ph, x, y, m, gv);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-        const C v = gr + ((C(cx(j)) - ux) * gx + (C(cy(j)) - uy) * gy) * inv;
+        const C v = gv[j];
         if (j > 0 && (m & (1u << (j - 1)))) {
             lam[opp(j) * g.nnode + n] = v;
         } else {
@@ -1498,23 +1536,29 @@ cudaError_t launch_reduce(const Geo &g, const Phys &ph, int phase, int kind, con
     k_reduce_final<P><<<1, AUX_BLOCK, 0, s>>>(partial, RED_BLOCKS, out);
     return cudaGetLastError();
 }
+template <int P, int F, bool OPEN>
+static void adjoint_rows(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
+                         void *grad_force, const Shape &sh, cudaStream_t s) {
+    for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
+        const dim3 grid(sh.gx, sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u);
+        k_adjoint<P, F, OPEN><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
+    }
+}
+template <int P, int F>
+static void adjoint_open(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
+                         void *grad_force, const Shape &sh, cudaStream_t s) {
+    if (ph.has_open) adjoint_rows<P, F, true>(g, ph, state, lam_in, lam_out, grad_force, sh, s);
+    else adjoint_rows<P, F, false>(g, ph, state, lam_in, lam_out, grad_force, sh, s);
+}
 template <int P>
 cudaError_t launch_adjoint(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
                            void *grad_force, cudaStream_t s) {
     const Shape sh = step_shape<StepVec<P, true>::value>(g); // dense, as k_adjoint
     if (sh.gx == 0) return cudaSuccess;
-    for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
-        const dim3 grid(sh.gx, sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u);
-        switch (ph.force_mode) {
-        case FORCE_NONE:
-            k_adjoint<P, FORCE_NONE><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
-            break;
-        case FORCE_UNIFORM:
-            k_adjoint<P, FORCE_UNIFORM><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
-            break;
-        default:
-            k_adjoint<P, FORCE_FIELD><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
-        }
+    switch (ph.force_mode) {
+    case FORCE_NONE: adjoint_open<P, FORCE_NONE>(g, ph, state, lam_in, lam_out, grad_force, sh, s); break;
+    case FORCE_UNIFORM: adjoint_open<P, FORCE_UNIFORM>(g, ph, state, lam_in, lam_out, grad_force, sh, s); break;
+    default: adjoint_open<P, FORCE_FIELD>(g, ph, state, lam_in, lam_out, grad_force, sh, s);
     }
     return cudaGetLastError();
 }

@@ -72,6 +72,31 @@ def test_adjoint_fp64_matches_oracle_chain(L, orc, T, K):
     assert np.all(g0[:, ~fl] == 0)
 
 
+def open_channel_case(nx=48, ny=32, seed=inputs.GEOMETRY_SEED + 3):
+    """Velocity inlet west, pressure outlet east, walls in y, cylinders."""
+    solid, _ = inputs.channel_cylinders(nx, ny, count=2, rmin=3, rmax=5, clearance=2, seed=seed)
+    solid[:, :2] = 0
+    solid[:, -2:] = 0
+    c = C.Case("openadj%dx%d" % (nx, ny), nx, ny, 0.8, px=False, py=False, walls={"north": (0.01, 0.0)},
+               solid=solid, open={"west": ("velocity", (0.02, 0.003)), "east": ("pressure", 1.001)})
+    c.rho0 = 1.0 + 0.01 * inputs.random_field((ny, nx), 94)
+    c.u0 = 0.02 * inputs.random_field((2, ny, nx), 95)
+    c.force_field = 1e-4 * inputs.random_field((2, ny, nx), 96)
+    return c
+
+
+@pytest.mark.parametrize("T,K", [(1, 1), (25, 6)])
+def test_adjoint_with_open_sides_fp64_matches_oracle_chain(L, orc, T, K):
+    c = open_channel_case()
+    ut = inputs.target_velocity(c.nx, c.ny, c.solid, amp=0.02)
+    A0, lam, gF, mask, loss = oracle_grads(orc, c, T, ut)
+    g0, gFg, lg, _ = gpu_grads(L, c, T, K, ut, "f64", A0)
+    fl = mask != 0xFF
+    assert abs(lg - loss) <= 1e-12 * abs(loss)
+    assert C.rel_l2(g0, lam, fl) <= 1e-10
+    assert C.rel_l2(gFg, gF, fl) <= 1e-10
+
+
 def test_adjoint_fp32_matches_oracle_chain(L, orc):
     c = channel_case()
     T = 40
