@@ -604,7 +604,7 @@ def adjoint_cost(nx=512, ny=256, T=2000, K=45, count=12, rmin=6, rmax=12):
             "grad_finite": bool(torch.isfinite(Fg.grad).all().item())}
 
 
-def _accuracy_runs(cases, steps, precisions, stream):
+def _accuracy_runs(cases, steps, precisions, stream, pattern="aa"):
     """For each case: GLUPS of each precision and the relative L2 norm of u
     over fluid nodes against the FP64 GPU run of the same case."""
     import torch
@@ -613,7 +613,7 @@ def _accuracy_runs(cases, steps, precisions, stream):
     for name, kw, r0, u0, nf, fl, layout in cases:
         ref_u = None
         for prec in ("f64",) + tuple(precisions):
-            sim = lbm.LBM(precision=prec, layout=layout, pattern="aa", **kw)
+            sim = lbm.LBM(precision=prec, layout=layout, pattern=pattern, **kw)
             sim.init_equilibrium(None if r0 is None else torch.as_tensor(r0, dtype=sim.dtype, device="cuda"),
                                  None if u0 is None else torch.as_tensor(u0, dtype=sim.dtype, device="cuda"))
             torch.cuda.synchronize()
@@ -628,7 +628,7 @@ def _accuracy_runs(cases, steps, precisions, stream):
             uu = uu.double()
             if fl is not None:
                 uu = uu * fl
-            entry = {"GLUPS": round(nf * steps / t / 1e9, 3), "layout": layout, "pattern": "aa"}
+            entry = {"GLUPS": round(nf * steps / t / 1e9, 3), "layout": layout, "pattern": pattern}
             if ref_u is None:
                 ref_u = uu
             else:
@@ -644,8 +644,9 @@ def _accuracy_runs(cases, steps, precisions, stream):
 def precision_sweep(n: int = 8192, steps: int = 5000):
     """Precision sweep: dense Taylor-Green (U 0.05) and the porous medium
     (phi 0.3, same disc generator, F = 1e-6) at n^2, FP64 vs FP32 vs FP16s
-    storage, `steps` steps each; plus the dense Taylor-Green and Poiseuille
-    boxes at 1024^2 .. 4096^2 after 1000 steps.  Errors are relative L2 norms
+    storage, `steps` steps each, in the in-place AA pattern; plus the dense
+    Taylor-Green and Poiseuille boxes at 1024^2 .. 4096^2 after 1000 steps,
+    two-lattice.  Errors are relative L2 norms
     of u over fluid nodes against the FP64 GPU run (itself pinned to the CPU
     oracle on the smaller configurations), reported beside GLUPS."""
     import torch
@@ -666,7 +667,7 @@ def precision_sweep(n: int = 8192, steps: int = 5000):
         fx, r, v = inputs.poiseuille(m, m, 0.8, 0.05)
         small.append(("poiseuille_%d" % m, dict(nx=m, ny=m, tau=0.8, force=(fx, 0.0), periodic_y=False),
                       r, v, m * m, None, "dense"))
-    res["steps_1000"] = _accuracy_runs(small, 1000, ("f32", "f16s"), stream)
+    res["steps_1000"] = _accuracy_runs(small, 1000, ("f32", "f16s"), stream, pattern="two_lattice")
     return {"sweep": "precision", "results": res}
 
 
