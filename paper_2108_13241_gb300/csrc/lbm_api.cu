@@ -336,6 +336,8 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
         ph.kq_hi[q] = (float)k;
         ph.kq_lo[q] = (float)(k - (double)ph.kq_hi[q]);
     }
+    ph.tau_h = 1.0 / ph.omega - 0.5;
+    ph.tau_h_f = (float)(1.0 / (double)ph.omega_f - 0.5);
     set_force_mode(c);
 
     lbm_status st = LBM_OK;

@@ -70,6 +70,10 @@ struct Phys {
     // for FP32 the float pair (hi + lo) of omega_f/3, omega_f/12
     double kq[2];
     float kq_hi[2], kq_lo[2];
+    // tau - 1/2 = (1 - omega/2) / omega: the Guo source's weight relative to
+    // the equilibrium's (FP64, and from omega_f for FP32 / FP16s)
+    double tau_h;
+    float tau_h_f;
     // open sides (lbm_side_kind per side; uniform values; optional per-node
     // values along the side, compute type)
     int has_open;

@@ -53,8 +53,8 @@ template <class C> __host__ __device__ constexpr C wgt(int i) {
 template <int P> struct St;
 // dec/enc convert between the stored element and f_i - w_i in the compute
 // type.  The step kernel works in units of SCALE (f_i - w_i times SCALE):
-// dec_step decodes into them, enc_sr (given 32 random bits) encodes from
-// them; every other kernel uses dec/enc.
+// dec_step decodes into them (FP16s encodes from them by dither and a
+// truncating conversion); every other kernel uses dec/enc.
 template <> struct St<LBM_F64> {
     typedef double R; // stored element
     typedef double C; // compute type
@@ -62,7 +62,6 @@ template <> struct St<LBM_F64> {
     static __device__ __forceinline__ C dec(R r) { return r; }
     static __device__ __forceinline__ C dec_step(R r) { return r; }
     static __device__ __forceinline__ R enc(C c) { return c; }
-    static __device__ __forceinline__ R enc_sr(C c, unsigned) { return c; }
 };
 template <> struct St<LBM_F32> {
     typedef float R;
@@ -71,12 +70,11 @@ template <> struct St<LBM_F32> {
     static __device__ __forceinline__ C dec(R r) { return r; }
     static __device__ __forceinline__ C dec_step(R r) { return r; }
     static __device__ __forceinline__ R enc(C c) { return c; }
-    static __device__ __forceinline__ R enc_sr(C c, unsigned) { return c; }
 };
 // FP16s: binary16 bits of (f_i - w_i) * 2^10.  The power-of-two scale is
 // exact; it moves the small deviations of slow flows (|f_i - w_i| down to
 // 6e-8) into binary16's normal range while keeping |f_i - w_i| up to 64
-// finite.  The time step rounds stochastically (enc_sr): the 13 mantissa
+// finite.  The time step rounds stochastically (dither): the 13 mantissa
 // bits that binary16 drops get 13 uniform random bits added before
 // truncation, so the rounding error has zero mean instead of repeating
 // itself step after step in a slowly varying flow.  Below binary16's normal
@@ -90,11 +88,20 @@ template <> struct St<LBM_F16S> {
     static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)) * (1.0f / 1024.0f); }
     static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c * 1024.0f)); }
     static __device__ __forceinline__ C dec_step(R r) { return __half2float(__ushort_as_half(r)); }
-    static __device__ __forceinline__ R enc_sr(C c, unsigned rnd) {
-        const unsigned b = __float_as_uint(c) + (rnd >> 19);
-        return __half_as_ushort(__float2half_rz(__uint_as_float(b)));
+    // c with 13 random bits added below binary16's last kept mantissa bit;
+    // truncating the result to binary16 rounds c stochastically
+    static __device__ __forceinline__ C dither(C c, unsigned rnd) {
+        return __uint_as_float(__float_as_uint(c) + (rnd >> 19));
     }
 };
+
+// Two values truncated to binary16 by one packed conversion: lo in the low
+// half of the word (the lower node index), hi in the high half.
+__device__ __forceinline__ unsigned f16x2_rz(float lo, float hi) {
+    unsigned r;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
 
 // Counter-based random bits for stochastic rounding: the 32-bit finaliser of
 // Appleby's MurmurHash3 applied to (node index, time step), then one
@@ -165,6 +172,17 @@ template <class R, int VEC> __device__ __forceinline__ void st16(R *p, const V16
 }
 template <class R, int VEC> __device__ __forceinline__ void zero16(V16<R, VEC> &v) {
     v.u = VecWord<(int)sizeof(R) * VEC>::zero();
+}
+// 32-bit word W of an 8- or 16-byte vector
+template <int W> __device__ __forceinline__ void set_word(uint2 &u, unsigned v) {
+    if (W == 0) u.x = v;
+    else u.y = v;
+}
+template <int W> __device__ __forceinline__ void set_word(uint4 &u, unsigned v) {
+    if (W == 0) u.x = v;
+    else if (W == 1) u.y = v;
+    else if (W == 2) u.z = v;
+    else u.w = v;
 }
 
 __device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(LBM_FULL, v, 1); }
@@ -360,6 +378,7 @@ template <> struct PC<double> {
     static __device__ __forceinline__ double omega(const Phys &p) { return p.omega; }
     static __device__ __forceinline__ double om1(const Phys &p) { return 1.0 - p.omega; }
     static __device__ __forceinline__ double kk(const Phys &p) { return 1.0 - 0.5 * p.omega; }
+    static __device__ __forceinline__ double tau_h(const Phys &p) { return p.tau_h; }
     static __device__ __forceinline__ double fx(const Phys &p) { return p.fx; }
     static __device__ __forceinline__ double fy(const Phys &p) { return p.fy; }
     static __device__ __forceinline__ double wt(const Phys &p, int s, int i) { return p.wt[s][i]; }
@@ -368,6 +387,7 @@ template <> struct PC<float> {
     static __device__ __forceinline__ float omega(const Phys &p) { return p.omega_f; }
     static __device__ __forceinline__ float om1(const Phys &p) { return p.om1_f; }
     static __device__ __forceinline__ float kk(const Phys &p) { return p.kk_f; }
+    static __device__ __forceinline__ float tau_h(const Phys &p) { return p.tau_h_f; }
     static __device__ __forceinline__ float fx(const Phys &p) { return p.fx_f; }
     static __device__ __forceinline__ float fy(const Phys &p) { return p.fy_f; }
     static __device__ __forceinline__ float wt(const Phys &p, int s, int i) { return p.wt_f[s][i]; }
@@ -401,8 +421,9 @@ __device__ __forceinline__ void moments_j(const C f[9], C Fx, C Fy, C &drho, C &
                                           C &jx, C &jy, C &jxl, C &jyl) {
     drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     rho = C(1) + drho * C(1.0 / SC);
-    const C mx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
-    const C my = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+    const C a = f[5] - f[7], b = f[8] - f[6];
+    const C mx = ((f[1] - f[3]) + a) + b;
+    const C my = ((f[2] - f[4]) + a) - b;
     inv = recip(rho) * C(1.0 / SC);
     jxl = jyl = C(0);
     if (HAS_F) {
@@ -428,10 +449,10 @@ __device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rh
 }
 
 template <class C> struct Coef {
-    C om, om1, kk;
+    C om, om1, kk, th;
     C kh[2], kl[2]; // omega/3, omega/12 (axis, diagonal); kl: low part (FP32)
     __device__ __forceinline__ explicit Coef(const Phys &ph)
-        : om(PC<C>::omega(ph)), om1(PC<C>::om1(ph)), kk(PC<C>::kk(ph)) {
+        : om(PC<C>::omega(ph)), om1(PC<C>::om1(ph)), kk(PC<C>::kk(ph)), th(PC<C>::tau_h(ph)) {
         if constexpr (sizeof(C) == 8) {
             kh[0] = C(ph.kq[0]);
             kh[1] = C(ph.kq[1]);
@@ -469,70 +490,94 @@ __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
     moments_j<C, HAS_F, COMP, SC>(f, Fx, Fy, drho, rho, inv, ux, uy, jx, jy, jxl, jyl);
     const C usq = C(1.5) * (ux * ux + uy * uy);
     const C om = co.om, om1 = co.om1;
-    // omega * w_q * rho (times SC) and omega * w_q * drho per weight class
     const C rs = rho * C(SC);
-    const C R0 = (om * C(4.0 / 9.0)) * rs, Ra = (om * C(1.0 / 9.0)) * rs, Rd = (om * C(1.0 / 36.0)) * rs;
-    const C E0 = (om * C(4.0 / 9.0)) * drho, Ea = (om * C(1.0 / 9.0)) * drho, Ed = (om * C(1.0 / 36.0)) * drho;
-    C uF = C(0), K0 = C(0), Ka = C(0), Kd = C(0);
-    if (HAS_F) {
-        uF = ux * Fx + uy * Fy;
-        const C ks = co.kk * C(SC);
-        K0 = ks * C(4.0 / 9.0);
-        Ka = ks * C(1.0 / 9.0);
-        Kd = ks * C(1.0 / 36.0);
-    }
-    // rest
-    {
-        C G = E0 - R0 * usq;
-        if (HAS_F) G = G + K0 * (C(-3) * uF);
-        f[0] = om1 * f[0] + G;
-    }
-    // one pair of opposite links: T = c_i . u, S = c_i . j (SL: its low part),
-    // CF = c_i . F, weight class Q (0 axis, 1 diagonal)
+    const C uF = HAS_F ? ux * Fx + uy * Fy : C(0);
+    if constexpr (COMP) {
+        // Guo source weights (1 - omega/2) w_q
+        C K0 = C(0), Ka = C(0), Kd = C(0);
+        if (HAS_F) {
+            K0 = co.kk * C(4.0 / 9.0);
+            Ka = co.kk * C(1.0 / 9.0);
+            Kd = co.kk * C(1.0 / 36.0);
+        }
+        // omega * w_q * rho and omega * w_q * drho per weight class
+        const C R0 = (om * C(4.0 / 9.0)) * rs, Ra = (om * C(1.0 / 9.0)) * rs, Rd = (om * C(1.0 / 36.0)) * rs;
+        const C E0 = (om * C(4.0 / 9.0)) * drho, Ea = (om * C(1.0 / 9.0)) * drho, Ed = (om * C(1.0 / 36.0)) * drho;
+        // rest
+        {
+            C G = E0 - R0 * usq;
+            if (HAS_F) G = G + K0 * (C(-3) * uF);
+            f[0] = om1 * f[0] + G;
+        }
+        // one pair of opposite links: T = c_i . u, S = c_i . j (SL: its low
+        // part), CF = c_i . F, weight class Q (0 axis, 1 diagonal)
 #define LBM_PAIR(I, J, T, SH, SL, CF, RQ, EQ, KQ, Q)                                        \
     {                                                                                       \
         const C t = (T);                                                                    \
         C P = EQ + RQ * (C(4.5) * (t * t) - usq);                                           \
-        C qh, ql = C(0);                                                                    \
-        if constexpr (COMP) {                                                               \
-            qh = rn_mul(co.kh[Q], (SH));                                                    \
-            ql = rn_add(rn_fma(co.kh[Q], (SH), -qh), rn_fma(co.kh[Q], (SL), rn_mul(co.kl[Q], (SH)))); \
-        } else if constexpr (sizeof(C) == 8) {                                              \
-            qh = co.kh[Q] * (SH);                                                           \
-        } else {                                                                            \
-            qh = co.kh[Q] * (SH);                                                           \
-            ql = co.kl[Q] * (SH);                                                           \
-        }                                                                                   \
+        const C qh = rn_mul(co.kh[Q], (SH));                                                \
+        C ql = rn_add(rn_fma(co.kh[Q], (SH), -qh), rn_fma(co.kh[Q], (SL), rn_mul(co.kl[Q], (SH)))); \
         if (HAS_F) {                                                                        \
             const C cf = (CF);                                                              \
             P = P + KQ * (C(9) * (t * cf) - C(3) * uF);                                     \
             ql = ql + (C(3) * KQ) * cf;                                                     \
         }                                                                                   \
-        C gp, gm;                                                                           \
-        if constexpr (COMP) {                                                               \
-            gp = rn_add(rn_add(P, qh), ql);                                                 \
-            gm = rn_sub(rn_sub(P, qh), ql);                                                 \
-        } else {                                                                            \
-            gp = (P + qh) + ql;                                                             \
-            gm = (P - qh) - ql;                                                             \
-        }                                                                                   \
-        f[I] = om1 * f[I] + gp;                                                             \
-        f[J] = om1 * f[J] + gm;                                                             \
+        f[I] = om1 * f[I] + rn_add(rn_add(P, qh), ql);                                      \
+        f[J] = om1 * f[J] + rn_sub(rn_sub(P, qh), ql);                                      \
     }
-    C sd1h = jx + jy, sd1l = C(0), sd2h = jy - jx, sd2l = C(0);
-    if constexpr (COMP) {
+        C sd1h, sd1l, sd2h, sd2l;
         two_sum(jx, jy, sd1h, sd1l);
         two_sum(jy, -jx, sd2h, sd2l);
         if (HAS_F) {
             sd1l = sd1l + (jxl + jyl);
             sd2l = sd2l + (jyl - jxl);
         }
-    }
-    LBM_PAIR(1, 3, ux, jx, jxl, Fx, Ra, Ea, Ka, 0)
-    LBM_PAIR(2, 4, uy, jy, jyl, Fy, Ra, Ea, Ka, 0)
-    LBM_PAIR(5, 7, ux + uy, sd1h, sd1l, Fx + Fy, Rd, Ed, Kd, 1)
-    LBM_PAIR(6, 8, uy - ux, sd2h, sd2l, Fy - Fx, Rd, Ed, Kd, 1)
+        LBM_PAIR(1, 3, ux, jx, jxl, Fx, Ra, Ea, Ka, 0)
+        LBM_PAIR(2, 4, uy, jy, jyl, Fy, Ra, Ea, Ka, 0)
+        LBM_PAIR(5, 7, ux + uy, sd1h, sd1l, Fx + Fy, Rd, Ed, Kd, 1)
+        LBM_PAIR(6, 8, uy - ux, sd2h, sd2l, Fy - Fx, Rd, Ed, Kd, 1)
 #undef LBM_PAIR
+    } else {
+        // FP64 and FP16s: the even part of omega (f^eq_i - w_i) is
+        // omega w_q (Z + 4.5 rho t^2) with Z = drho - rho usq, one product
+        // per link pair on top of t^2 (FP64 is bound by its FP64 pipe, FP16s
+        // by instruction issue); the odd part, 3 omega w_q (c_i . j), is one
+        // value q that the pair adds and subtracts (FP16s: the constant as a
+        // float pair, kh S + kl S).  With a force, the Guo source joins both
+        // parts per node instead of per link: with h = tau - 1/2,
+        //   even: omega w_q (Z - 3 h (u . F) + 4.5 t (c_i . (j + 2 h F)))
+        //   odd:  3 omega w_q (c_i . (j + h F)),
+        // which is Eq. 6 and the source term, regrouped.
+        C Z = drho - rs * usq;
+        const C r45 = C(4.5) * rs;
+        const C w0 = om * C(4.0 / 9.0), wa = om * C(1.0 / 9.0), wd = om * C(1.0 / 36.0);
+        C vx = jx, vy = jy, kx = jx, ky = jy;
+        if (HAS_F) {
+            const C h = co.th * C(SC);
+            Z = Z - (C(3) * h) * uF;
+            kx = jx + h * Fx;
+            ky = jy + h * Fy;
+            vx = jx + (C(2) * h) * Fx;
+            vy = jy + (C(2) * h) * Fy;
+        }
+        f[0] = om1 * f[0] + w0 * Z;
+#define LBM_PAIR(I, J, T, TV, SK, WQ, Q)                                                    \
+    {                                                                                       \
+        const C t = (T);                                                                    \
+        C y;                                                                                \
+        if (HAS_F) y = Z + (C(4.5) * t) * (TV);                                             \
+        else y = Z + r45 * (t * t);                                                         \
+        C q = co.kh[Q] * (SK);                                                              \
+        if constexpr (sizeof(C) == 4) q = q + co.kl[Q] * (SK);                              \
+        f[I] = om1 * f[I] + (WQ * y + q);                                                   \
+        f[J] = om1 * f[J] + (WQ * y - q);                                                   \
+    }
+        LBM_PAIR(1, 3, ux, vx, kx, wa, 0)
+        LBM_PAIR(2, 4, uy, vy, ky, wa, 0)
+        LBM_PAIR(5, 7, ux + uy, vx + vy, kx + ky, wd, 1)
+        LBM_PAIR(6, 8, uy - ux, vy - vx, ky - kx, wd, 1)
+#undef LBM_PAIR
+    }
 }
 
 // Discrete adjoint of one node's collision (see the oracle's derivation):
@@ -817,32 +862,61 @@ __device__ __forceinline__ void load_force(const Geo &g, const Phys &ph, const A
     }
 }
 
+// Stochastic rounding of the thread's nodes: the per-step seed, and the
+// dithered values of the even node of a pair until its odd partner is done.
+struct SrState {
+    unsigned tseed;
+    float pend[9];
+};
+
+// Stores node K's nine dithered FP16s values: nodes 2j and 2j+1 share a
+// 32-bit word of each slot vector and are truncated together, except in the
+// AA gather/scatter step, whose x-shifted slots are stored value by value
+// (there one conversion per value measured faster).
+template <class S, int MODE, int K>
+__device__ __forceinline__ void put_sr(const float d[9], SrState &sr, V16<typename S::R, S::VEC> out[9]) {
+    constexpr bool PAIRS = MODE != MODE_AA_PULLPUSH;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if constexpr (!PAIRS) out[i].v[K] = __half_as_ushort(__float2half_rz(d[i]));
+        else if constexpr ((K & 1) == 0 && K + 1 < S::VEC) sr.pend[i] = d[i];
+        else if constexpr ((K & 1) == 1) set_word<K / 2>(out[i].u, f16x2_rz(sr.pend[i], d[i]));
+        else out[i].v[K] = __half_as_ushort(__float2half_rz(d[i]));
+    }
+}
+
 template <class S, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, int K>
 __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                         const V16<typename S::R, S::VEC> own[9],
                                         unsigned long long mv, const V16<typename S::R, S::VEC> raw[9],
                                         const typename S::R edge[9], const typename S::C Fx[],
-                                        const typename S::C Fy[], const Coef<typename S::C> &co, unsigned tseed,
+                                        const typename S::C Fy[], const Coef<typename S::C> &co, SrState &sr,
                                         V16<typename S::R, S::VEC> out[9]) {
     typedef typename S::C C;
     C f[9];
     node_values<S, K, MODE>(raw, edge, f);
     const unsigned m = HAS_MASK ? (unsigned)((mv >> (8 * K)) & 0xFFu) : 0u;
     if (HAS_MASK && m == 0xFFu) {
+        if constexpr (S::STOCHASTIC) {
+            const float z[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            put_sr<S, MODE, K>(z, sr, out);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(C(0));
+            for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(C(0));
+        }
         return;
     }
     if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, src, raw, own, K, m, f);
     if constexpr (OPEN) apply_open<C, S::SCALE>(g, ph, ad.gx(K), ad.gy(), m, f);
     collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE>(f, Fx[K], Fy[K], co);
     if constexpr (S::STOCHASTIC) {
-        unsigned h = fmix32((unsigned)ad.node(K) ^ tseed);
+        unsigned h = fmix32((unsigned)ad.node(K) ^ sr.tseed);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             h = lcg_next(h);
-            out[i].v[K] = S::enc_sr(f[i], h);
+            f[i] = S::dither(f[i], h);
         }
+        put_sr<S, MODE, K>(f, sr, out);
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);
@@ -858,12 +932,11 @@ struct NodeRange {
                                                const V16<typename S::R, S::VEC> raw[9],
                                                const typename S::R edge[9], const typename S::C Fx[],
                                                const typename S::C Fy[], const Coef<typename S::C> &co,
-                                               unsigned tseed, V16<typename S::R, S::VEC> out[9]) {
+                                               SrState &sr, V16<typename S::R, S::VEC> out[9]) {
         if constexpr (K < K1) {
-            do_node<S, A, MODE, HAS_MASK, FORCE, OPEN, K>(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed,
-                                                          out);
+            do_node<S, A, MODE, HAS_MASK, FORCE, OPEN, K>(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr, out);
             NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, K + 1, K1>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy,
-                                                                         co, tseed, out);
+                                                                         co, sr, out);
         }
     }
 };
@@ -945,9 +1018,9 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
     const Coef<C> co(ph);
 
     V16<R, VEC> out[9];
-    const unsigned tseed = S::STOCHASTIC ? fmix32(step * 0x9E3779B9u + 0x632BE5ABu) : 0u;
-    NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, 0, VEC>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, tseed,
-                                                             out);
+    SrState sr;
+    sr.tseed = S::STOCHASTIC ? fmix32(step * 0x9E3779B9u + 0x632BE5ABu) : 0u;
+    NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, 0, VEC>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr, out);
     store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
 }
 
