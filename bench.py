@@ -219,7 +219,6 @@ def run_gpu_arm(args, rank, world, dist):
     stream = torch.cuda.current_stream()
     kw, rho, u, nfluid, wname = build_case(args.workload, args.n, args.precision)
     sim = lbm.LBM(precision=args.precision, layout=args.layout, pattern=args.pattern, **kw)
-    launches_per_step = sim.launches_per_step
     dtype = sim.dtype
     rho_h = None if rho is None else torch.as_tensor(rho, dtype=dtype).pin_memory()
     u_h = None if u is None else torch.as_tensor(u, dtype=dtype).pin_memory()
@@ -244,6 +243,9 @@ def run_gpu_arm(args, rank, world, dist):
         end.record(stream)
         end.synchronize()
     barrier()
+    # kernels of the timed sim.step(K): K x launches per step (graph nodes
+    # included), plus the step counter's set and advances when graphs replay
+    step_launches = sim.step_launches(args.steps)
     t = max_over_ranks(start.elapsed_time(end) / 1e3, dist, dev)
     clocks = clk.summary()
     mass, _ = sim.reduce()
@@ -297,7 +299,7 @@ def run_gpu_arm(args, rank, world, dist):
                 "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
                 "what": "pinned host rho,u -> device, lbm_init_equilibrium, K x lbm_step, lbm_macros, "
                         "device -> pinned host rho,u"},
-        "gpu_launches": args.steps * launches_per_step,
+        "gpu_launches": step_launches,
         "clocks": clocks,
     }
     sim.close()

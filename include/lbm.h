@@ -162,8 +162,18 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *d_rho, const void *d_u
 /* n time steps of Algorithm 1 (n >= 0): per fluid node, pull gather with
  * bounce-back, moments (Eq. 2, u shifted by F/2), f^eq (Eq. 6), BGK
  * relaxation (Eq. 3, Eq. 4) plus the Guo source
- * (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F, aligned store. */
+ * (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F, aligned store.
+ * With graphs enabled (the default, lbm_set_graphs), runs of 32 steps or
+ * more are replayed from a CUDA graph recorded on the first such call (the
+ * same kernels and arguments, so the results are bit-identical); the graph
+ * is recorded again after lbm_set_force or lbm_set_side_values. */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Whether lbm_step, lbm_forward_states and lbm_backward replay CUDA graphs
+ * (enable != 0, the default) or issue every kernel launch from the host.
+ * Launch-bound runs (small grids) gain from the graphs; a context whose
+ * graph could not be recorded switches to direct launches by itself. */
+lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
 
 /* Density and velocity of the current state (Eq. 2 on the gathered f'
  * of the next step, u = (m + F/2)/rho).  d_rho [ny][nx], d_u [2][ny][nx]
@@ -198,7 +208,8 @@ lbm_status lbm_load_state(lbm_ctx *ctx, const void *d_src);
  * h_states is a HOST array of n+1 device pointers; t0 is the step index of
  * d_states[0] (FP16s stochastic rounding then reproduces the original run).
  * The context's own lattice and step counter are not touched.  Two-lattice
- * only. */
+ * only.  Runs of 8 steps or more replay a CUDA graph, recorded again when
+ * n or a pointer of h_states changes (see lbm_set_graphs). */
 lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long long t0);
 
 /* Discrete adjoint of n steps (transpose of the linearised Algorithm 1
@@ -208,7 +219,8 @@ lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long l
  * d_lambda_tmp: same size, scratch.  d_grad_force [2][ny][nx] compute type,
  * accumulated (+=): dL/dF(x) for the per-node force (the uniform force's
  * gradient is its node sum).  Entries of solid nodes come out 0.
- * LBM_ERR_UNSUPPORTED unless dense and two-lattice. */
+ * LBM_ERR_UNSUPPORTED unless dense and two-lattice.  Runs of 8 steps or
+ * more replay a CUDA graph, recorded again when n or a pointer changes. */
 lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n,
                         void *d_lambda, void *d_lambda_tmp, void *d_grad_force);
 
@@ -266,6 +278,12 @@ long long lbm_step_count(const lbm_ctx *ctx);
  * when the dense grid runs its boundary rows with the masked kernel and the
  * rest without, more for grids of over 65535 rows).  -1 for a NULL ctx. */
 int lbm_launches_per_step(const lbm_ctx *ctx);
+
+/* Kernel launches (graph nodes included) that lbm_step(ctx, n) makes now:
+ * n * lbm_launches_per_step, plus, when graphs replay, one to set the
+ * device step counter and one per 32-step replay to advance it.  -1 for a
+ * NULL ctx or n < 0. */
+long long lbm_step_launches(const lbm_ctx *ctx, int n);
 const char *lbm_status_string(lbm_status s);
 const char *lbm_last_error(const lbm_ctx *ctx);
 

@@ -72,10 +72,14 @@ class LBMFunction(torch.autograd.Function):
         sim.load_state(ctx.final)
         sim.macros_backward(None if g_rho is None else g_rho.contiguous(),
                             None if g_u is None else g_u.contiguous(), lam, gF)
-        bufs = [sim.new_state() for _ in range(max(0, ctx.K - 1))]
+        # every segment runs on the same K state buffers (the checkpoint is
+        # copied into the first), so that the recompute and the adjoint sweep
+        # of all full segments replay one recorded CUDA graph each
+        bufs = [sim.new_state() for _ in range(max(1, ctx.K))]
         for s in range(len(ctx.segs) - 1, -1, -1):
             start, n = ctx.segs[s]
-            states = [ctx.ckpts[s]] + bufs[: n - 1]
+            bufs[0].copy_(ctx.ckpts[s])
+            states = bufs[:n]
             if n > 1:
                 sim.forward_states(states, ctx.t_start + start)
             sim.backward(states, lam, lam_tmp, gF)

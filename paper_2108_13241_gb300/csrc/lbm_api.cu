@@ -8,6 +8,14 @@
 //   AA: one lattice.  PH_SWAPPED: slot opp(i) of x holds A_i(x).  A
 //     gather/scatter step moves it to PH_STREAMED (slot i of x holds the
 //     pulled f'_i(x) of the next step); a local step moves it back.
+//
+// Launch-bound runs (small grids: a step's kernel takes about as long as the
+// host needs to issue it) replay recorded CUDA graphs: lbm_step in chunks of
+// GRAPH_CHUNK steps, lbm_forward_states and lbm_backward as a whole once they
+// are GRAPH_MIN steps or longer.  A graph is recorded once and replayed while
+// the pointers and physics it was recorded with stay the same (the autograd
+// segments reuse their state buffers, so every full segment replays); the
+// FP16s steps of a graph read their time-step index from a device counter.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +46,15 @@ struct lbm_ctx {
     cudaStream_t stream;
     lbm_status sticky;
     std::string err;
+    // CUDA graphs (see the top of this file)
+    struct GraphCache {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<unsigned long long> key;
+    } gc[4];
+    cudaStream_t cap = nullptr;       // stream the graphs are recorded on
+    int graphs = 1;                   // replay graphs (lbm_set_graphs)
+    unsigned long long *tb = nullptr; // device time-step counter of replayed steps
+    unsigned long long version = 0;   // bumped when the physics' pointers change
 };
 
 namespace {
@@ -87,7 +104,7 @@ struct Plan {
     int ntiles, ntx, nty;
     bool has_mask;
     long long nslot;
-    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_list2, off_list4, total;
+    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_tb, off_list2, off_list4, total;
     size_t lat_bytes, mask_bytes;
     bool use_list;
 };
@@ -160,6 +177,8 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
     off += align256((size_t)RED_BLOCKS * 4 * sizeof(double));
     pl.off_out = off;
     off += align256(4 * sizeof(double));
+    pl.off_tb = off;
+    off += align256(sizeof(unsigned long long));
     // the list pays off when a good part of the kept tiles' vectors is solid
     // (measured on 4096^2 disc media: +10-33% at 42% active vectors, -3% at 87%)
     pl.use_list = p.layout == LBM_SPARSE_TILE16 && pl.ntiles > 0 &&
@@ -207,6 +226,105 @@ void set_force_mode(lbm_ctx *c) {
 
 void *current_lattice(lbm_ctx *c) { return c->p.pattern == LBM_AA ? c->lat[0] : c->lat[c->cur]; }
 int current_phase(lbm_ctx *c) { return c->p.pattern == LBM_AA ? c->phase : PH_PLAIN; }
+
+// One time step from lattice state (cur, phase), which it advances; t is the
+// step's index (or its offset from *ph.tbase).
+cudaError_t launch_one_step(lbm_ctx *c, const Phys &ph, int &cur, int &phase, unsigned long long t,
+                            cudaStream_t s) {
+    cudaError_t e;
+    if (c->p.pattern == LBM_TWO_LATTICE) {
+        e = LBM_DISPATCH(c->p.precision,
+                         launch_step<P>(c->geo, ph, MODE_TWO_LATTICE, c->lat[cur], c->lat[1 - cur], t, s));
+        cur = 1 - cur;
+    } else {
+        const int mode = phase == PH_SWAPPED ? MODE_AA_PULLPUSH : MODE_AA_LOCAL;
+        e = LBM_DISPATCH(c->p.precision, launch_step<P>(c->geo, ph, mode, c->lat[0], c->lat[0], t, s));
+        phase = phase == PH_SWAPPED ? PH_STREAMED : PH_SWAPPED;
+    }
+    return e;
+}
+
+// ---- CUDA graphs
+
+// cache slots: lbm_step's chunk from either lattice parity (a run of odd
+// length leaves the other one), the recompute, the adjoint sweep
+enum { GC_STEP = 0, GC_FWD = 2, GC_BWD = 3 };
+constexpr int GRAPH_CHUNK = 32; // steps per replay of lbm_step's graph (even)
+constexpr int GRAPH_MIN = 8;    // shortest forward_states / backward run recorded
+
+__global__ void k_counter(unsigned long long *c, unsigned long long v, int add) {
+    if (add) *c += v;
+    else *c = v;
+}
+cudaError_t set_counter(unsigned long long *c, unsigned long long v, cudaStream_t s) {
+    k_counter<<<1, 1, 0, s>>>(c, v, 0);
+    return cudaGetLastError();
+}
+
+// Destroys the recorded graphs (after the work they may have in flight).
+void drop_graphs(lbm_ctx *c) {
+    bool any = false;
+    for (auto &g : c->gc) any = any || g.exec;
+    if (!any) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &g : c->gc) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.key.clear();
+    }
+}
+
+// A graph could not be recorded or launched: clear the (non-sticky) error and
+// issue this context's launches directly from now on.
+void graphs_failed(lbm_ctx *c) {
+    cudaGetLastError();
+    c->graphs = 0;
+}
+
+// Launches cache slot `which`, recording it first with record(stream) when
+// its key differs from the one it was recorded with.
+template <class F>
+cudaError_t replay(lbm_ctx *c, int which, const std::vector<unsigned long long> &key, F record) {
+    lbm_ctx::GraphCache &gc = c->gc[which];
+    if (!gc.exec || gc.key != key) {
+        if (gc.exec) {
+            cudaStreamSynchronize(c->stream); // the old graph may still run
+            cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+            gc.key.clear();
+        }
+        cudaError_t e = cudaSuccess;
+        if (!c->cap) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const cudaError_t er = record(c->cap);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(c->cap, &graph);
+        if (er != cudaSuccess) e = er;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            return e;
+        }
+        gc.key = key;
+    }
+    return cudaGraphLaunch(gc.exec, c->stream);
+}
+
+// GRAPH_CHUNK steps from the context's (cur, phase), time-step indices read
+// from the device counter, which the last node advances by GRAPH_CHUNK.
+cudaError_t record_steps(lbm_ctx *c, cudaStream_t s) {
+    Phys ph = c->phys;
+    ph.tbase = c->tb;
+    int cur = c->cur, phase = c->phase;
+    for (int j = 0; j < GRAPH_CHUNK; ++j) {
+        const cudaError_t e = launch_one_step(c, ph, cur, phase, (unsigned long long)j, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_counter<<<1, 1, 0, s>>>(c->tb, (unsigned long long)GRAPH_CHUNK, 1);
+    return cudaGetLastError();
+}
 
 } // namespace
 
@@ -268,6 +386,7 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     c->lat[1] = p->pattern == LBM_TWO_LATTICE ? ws + pl.off_lat1 : ws;
     c->partial = reinterpret_cast<double *>(ws + pl.off_part);
     c->red_out = reinterpret_cast<double *>(ws + pl.off_out);
+    c->tb = reinterpret_cast<unsigned long long *>(ws + pl.off_tb);
     c->cur = 0;
     c->phase = p->pattern == LBM_AA ? PH_SWAPPED : PH_PLAIN;
     c->steps = 0;
@@ -403,7 +522,15 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
 
 lbm_status lbm_destroy(lbm_ctx *ctx) {
     if (!ctx) return LBM_ERR_INVALID;
+    drop_graphs(ctx);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable) {
+    LBM_CTX_CHECK(ctx);
+    ctx->graphs = enable != 0;
     return LBM_OK;
 }
 
@@ -413,6 +540,7 @@ lbm_status lbm_set_side_values(lbm_ctx *ctx, int side, const void *d_values) {
         return fail(ctx, LBM_ERR_INVALID, "side is not open");
     if (d_values && ((uintptr_t)d_values % ctx->csize)) return fail(ctx, LBM_ERR_INVALID, "values not aligned");
     ctx->phys.open_val[side] = d_values;
+    ++ctx->version;
     return LBM_OK;
 }
 
@@ -421,6 +549,7 @@ lbm_status lbm_set_force(lbm_ctx *ctx, const void *d_force) {
     if (d_force && ((uintptr_t)d_force & 15)) return fail(ctx, LBM_ERR_INVALID, "force not 16-byte aligned");
     ctx->phys.force = d_force;
     set_force_mode(ctx);
+    ++ctx->version;
     return LBM_OK;
 }
 
@@ -437,21 +566,25 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const void *d_rho, const void *d_u
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
     LBM_CTX_CHECK(ctx);
     if (n < 0) return fail(ctx, LBM_ERR_INVALID, "negative step count");
-    const Geo &g = ctx->geo;
-    for (int k = 0; k < n; ++k) {
-        cudaError_t e;
-        if (ctx->p.pattern == LBM_TWO_LATTICE) {
-            const void *a = ctx->lat[ctx->cur];
-            void *b = ctx->lat[1 - ctx->cur];
-            e = LBM_DISPATCH(ctx->p.precision, launch_step<P>(g, ctx->phys, MODE_TWO_LATTICE, a, b,
-                                                              (unsigned long long)ctx->steps, ctx->stream));
-            ctx->cur = 1 - ctx->cur;
-        } else {
-            const int mode = ctx->phase == PH_SWAPPED ? MODE_AA_PULLPUSH : MODE_AA_LOCAL;
-            e = LBM_DISPATCH(ctx->p.precision, launch_step<P>(g, ctx->phys, mode, ctx->lat[0], ctx->lat[0],
-                                                              (unsigned long long)ctx->steps, ctx->stream));
-            ctx->phase = ctx->phase == PH_SWAPPED ? PH_STREAMED : PH_SWAPPED;
+    int k = 0;
+    if (ctx->graphs && n >= GRAPH_CHUNK) {
+        cudaError_t e = set_counter(ctx->tb, (unsigned long long)ctx->steps, ctx->stream);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "step counter");
+        const std::vector<unsigned long long> key = {(unsigned long long)ctx->cur, (unsigned long long)ctx->phase,
+                                                     ctx->version};
+        const int slot = GC_STEP + (ctx->p.pattern == LBM_AA ? (ctx->phase == PH_SWAPPED ? 0 : 1) : ctx->cur);
+        for (; k + GRAPH_CHUNK <= n; k += GRAPH_CHUNK) {
+            e = replay(ctx, slot, key, [ctx](cudaStream_t s) { return record_steps(ctx, s); });
+            if (e != cudaSuccess) {
+                graphs_failed(ctx);
+                break;
+            }
+            ctx->steps += GRAPH_CHUNK; // an even chunk: cur and phase are back
         }
+    }
+    for (; k < n; ++k) {
+        const cudaError_t e =
+            launch_one_step(ctx, ctx->phys, ctx->cur, ctx->phase, (unsigned long long)ctx->steps, ctx->stream);
         if (e != cudaSuccess) return cuda_check(ctx, e, "step kernel");
         ++ctx->steps;
     }
@@ -556,6 +689,27 @@ lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long l
     for (int k = 0; k < n; ++k) {
         if (!h_states[k] || !h_states[k + 1] || ((uintptr_t)h_states[k] & 15) || ((uintptr_t)h_states[k + 1] & 15))
             return fail(ctx, LBM_ERR_INVALID, "bad state pointer");
+    }
+    if (ctx->graphs && n >= GRAPH_MIN) {
+        std::vector<unsigned long long> key = {(unsigned long long)n, ctx->version};
+        for (int k = 0; k <= n; ++k) key.push_back((unsigned long long)(uintptr_t)h_states[k]);
+        cudaError_t e = set_counter(ctx->tb, (unsigned long long)t0, ctx->stream);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "step counter");
+        e = replay(ctx, GC_FWD, key, [ctx, h_states, n](cudaStream_t s) {
+            Phys ph = ctx->phys;
+            ph.tbase = ctx->tb;
+            for (int k = 0; k < n; ++k) {
+                const cudaError_t r = LBM_DISPATCH(ctx->p.precision,
+                                                   launch_step<P>(ctx->geo, ph, MODE_TWO_LATTICE, h_states[k],
+                                                                  h_states[k + 1], (unsigned long long)k, s));
+                if (r != cudaSuccess) return r;
+            }
+            return cudaSuccess;
+        });
+        if (e == cudaSuccess) return LBM_OK;
+        graphs_failed(ctx);
+    }
+    for (int k = 0; k < n; ++k) {
         cudaError_t e = LBM_DISPATCH(ctx->p.precision,
                                      launch_step<P>(ctx->geo, ctx->phys, MODE_TWO_LATTICE, h_states[k],
                                                     h_states[k + 1], (unsigned long long)(t0 + k), ctx->stream));
@@ -573,20 +727,35 @@ lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n, void *
         return fail(ctx, LBM_ERR_INVALID, "bad backward arguments");
     if (((uintptr_t)d_lambda & 15) || ((uintptr_t)d_lambda_tmp & 15) || ((uintptr_t)d_grad_force & 15))
         return fail(ctx, LBM_ERR_INVALID, "buffers must be 16-byte aligned");
-    void *in = d_lambda, *out = d_lambda_tmp;
-    for (int t = n - 1; t >= 0; --t) {
+    for (int t = 0; t < n; ++t)
         if (!h_states[t]) return fail(ctx, LBM_ERR_INVALID, "NULL state");
-        cudaError_t e = LBM_DISPATCH(ctx->p.precision, launch_adjoint<P>(ctx->geo, ctx->phys, h_states[t], in,
-                                                                         out, d_grad_force, ctx->stream));
-        if (e != cudaSuccess) return cuda_check(ctx, e, "adjoint kernel");
-        void *tmp = in;
-        in = out;
-        out = tmp;
+    // the n adjoint steps, lambda ping-ponging between the two buffers and
+    // ending in d_lambda
+    auto sweep = [ctx, h_states, n, d_lambda, d_lambda_tmp, d_grad_force](cudaStream_t s) {
+        void *in = d_lambda, *out = d_lambda_tmp;
+        for (int t = n - 1; t >= 0; --t) {
+            const cudaError_t e = LBM_DISPATCH(ctx->p.precision, launch_adjoint<P>(ctx->geo, ctx->phys, h_states[t],
+                                                                                   in, out, d_grad_force, s));
+            if (e != cudaSuccess) return e;
+            void *tmp = in;
+            in = out;
+            out = tmp;
+        }
+        if (in != d_lambda)
+            return cudaMemcpyAsync(d_lambda, in, (size_t)9 * ctx->geo.nnode * ctx->csize, cudaMemcpyDeviceToDevice,
+                                   s);
+        return cudaSuccess;
+    };
+    if (ctx->graphs && n >= GRAPH_MIN) {
+        std::vector<unsigned long long> key = {(unsigned long long)n, ctx->version,
+                                               (unsigned long long)(uintptr_t)d_lambda,
+                                               (unsigned long long)(uintptr_t)d_lambda_tmp,
+                                               (unsigned long long)(uintptr_t)d_grad_force};
+        for (int t = 0; t < n; ++t) key.push_back((unsigned long long)(uintptr_t)h_states[t]);
+        if (replay(ctx, GC_BWD, key, sweep) == cudaSuccess) return LBM_OK;
+        graphs_failed(ctx);
     }
-    if (in != d_lambda)
-        return cuda_check(ctx, cudaMemcpyAsync(d_lambda, in, (size_t)9 * ctx->geo.nnode * ctx->csize,
-                                               cudaMemcpyDeviceToDevice, ctx->stream), "lambda copy");
-    return LBM_OK;
+    return cuda_check(ctx, sweep(ctx->stream), "adjoint kernel");
 }
 
 lbm_status lbm_macros_backward(lbm_ctx *ctx, const void *d_grad_rho, const void *d_grad_u, void *d_lambda,
@@ -645,6 +814,12 @@ int lbm_launches_per_step(const lbm_ctx *ctx) {
     if (g.layout != LBM_DENSE) return 1;
     if (g.has_mask && g.frame_y) return 1 + (g.ny - 2 + 65534) / 65535;
     return (g.ny + 65534) / 65535;
+}
+long long lbm_step_launches(const lbm_ctx *ctx, int n) {
+    if (!ctx || n < 0) return -1;
+    const long long per = lbm_launches_per_step(ctx);
+    if (!ctx->graphs || n < GRAPH_CHUNK) return per * n;
+    return per * n + 1 + n / GRAPH_CHUNK; // + the counter's set and one add per replay
 }
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 

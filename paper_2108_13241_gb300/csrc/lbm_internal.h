@@ -74,6 +74,9 @@ struct Phys {
     // the equilibrium's (FP64, and from omega_f for FP32 / FP16s)
     double tau_h;
     float tau_h_f;
+    // when set, the step kernel's time-step index is *tbase + its step
+    // argument (steps replayed from a CUDA graph, whose arguments are fixed)
+    const unsigned long long *tbase;
     // open sides (lbm_side_kind per side; uniform values; optional per-node
     // values along the side, compute type)
     int has_open;

@@ -1031,7 +1031,12 @@ __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const 
 
     V16<R, VEC> out[9];
     SrState sr;
-    sr.tseed = S::STOCHASTIC ? fmix32(step * 0x9E3779B9u + 0x632BE5ABu) : 0u;
+    if constexpr (S::STOCHASTIC) {
+        const unsigned t = ph.tbase ? (unsigned)__ldg(ph.tbase) + step : step;
+        sr.tseed = fmix32(t * 0x9E3779B9u + 0x632BE5ABu);
+    } else {
+        sr.tseed = 0u;
+    }
     NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, 0, VEC>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr, out);
     store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
 }

@@ -102,6 +102,8 @@ def _load():
         "lbm_fluid_nodes": ([_vp], ctypes.c_longlong),
         "lbm_step_count": ([_vp], ctypes.c_longlong),
         "lbm_launches_per_step": ([_vp], ctypes.c_int),
+        "lbm_set_graphs": ([_vp, ctypes.c_int], st),
+        "lbm_step_launches": ([_vp, ctypes.c_int], ctypes.c_longlong),
         "lbm_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lbm_last_error": ([_vp], ctypes.c_char_p),
     }
@@ -176,6 +178,14 @@ def lbm_init_equilibrium(ctx, rho: Optional[torch.Tensor], u: Optional[torch.Ten
 
 def lbm_step(ctx, n: int):
     _check("lbm_step", _load().lbm_step(ctx, int(n)), ctx)
+
+
+def lbm_set_graphs(ctx, enable: bool):
+    _check("lbm_set_graphs", _load().lbm_set_graphs(ctx, int(bool(enable))), ctx)
+
+
+def lbm_step_launches(ctx, n: int) -> int:
+    return _load().lbm_step_launches(ctx, int(n))
 
 
 def lbm_macros(ctx, rho: Optional[torch.Tensor], u: Optional[torch.Tensor]):
@@ -397,6 +407,15 @@ class LBM:
     @property
     def launches_per_step(self) -> int:
         return _load().lbm_launches_per_step(self.ctx)
+
+    def step_launches(self, n: int) -> int:
+        """Kernel launches that step(n) makes (graph nodes included)."""
+        return lbm_step_launches(self.ctx, n)
+
+    def set_graphs(self, enable: bool):
+        """Replay CUDA graphs for long step runs (default) or launch every
+        kernel from the host."""
+        lbm_set_graphs(self.ctx, enable)
 
     def _t(self, a, shape):
         t = torch.as_tensor(a, dtype=self.dtype, device=self.device).contiguous()
