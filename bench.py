@@ -75,19 +75,45 @@ def kernel_hash() -> str:
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
-def profiled_traffic(name: str):
-    """DRAM bytes per launch recorded in profiles/<name>.md by an ncu capture of
-    the current kernel source (None when absent or taken on another source)."""
+def profiled_value(name: str, key: str):
+    """A figure ("key: value" line) recorded in profiles/<name>.md by an ncu
+    capture of the current kernel source (None when absent or taken on
+    another source)."""
     path = os.path.join(PROFILE_DIR, name + ".md")
     try:
         text = open(path).read()
     except OSError:
         return None
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
     if not h or not t or h.group(1) != kernel_hash():
         return None
     return float(t.group(1))
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the profiled kernel (see profiled_value)."""
+    return profiled_value(name, "dram_bytes_per_launch")
+
+
+# FP64 pipe of GB300: 2 FP64 thread instructions per SM per cycle (ncu's
+# sm__sass_thread_inst_executed_op_dfma_pred_on.peak_sustained, 304 per cycle
+# over the 152 SMs), at the 2070 MHz maximum SM clock
+FP64_PER_SM_CYCLE = 2
+SM_MAX_HZ = 2070e6
+
+
+def fp64_alu_roofline(glups: float, sms: int):
+    """The FP64 step is bound by the FP64 pipe, not by HBM: its ceiling is the
+    pipe's instruction rate over the FP64 instructions one node update issues
+    (from the committed ncu capture of the dense FP64 step)."""
+    per_node = profiled_value("step_f64_dense_two_lattice_taylor_green_2048", "fp64_thread_instructions_per_node")
+    if per_node is None:
+        return None
+    peak = FP64_PER_SM_CYCLE * sms * SM_MAX_HZ
+    ceiling = peak / per_node / 1e9
+    return {"bound": "alu", "fp64_inst_per_node": per_node, "peak_fp64_inst_per_s": peak,
+            "GLUPS_ceiling": round(ceiling, 3), "frac": round(glups / ceiling, 4)}
 
 
 class ClockSampler:
@@ -443,8 +469,13 @@ def extra_measurements(args):
                                      ("f16s", "dense", "aa", 500), ("f32", "sparse", "two_lattice", 500),
                                      ("f32", "sparse", "aa", 500), ("f16s", "sparse", "aa", 500)]:
         t = run(kw, rho, u, prec, layout, pattern, k)
-        dense_geom[(prec, layout, pattern)] = record("taylor_green_%d/%s/%s/%s" % (n, prec, layout, pattern),
-                                                     n * n, k, t, prec)
+        key = "taylor_green_%d/%s/%s/%s" % (n, prec, layout, pattern)
+        dense_geom[(prec, layout, pattern)] = record(key, n * n, k, t, prec)
+        if prec == "f64":
+            alu = fp64_alu_roofline(dense_geom[(prec, layout, pattern)],
+                                    torch.cuda.get_device_properties(0).multi_processor_count)
+            if alu is not None:
+                out[key]["alu_roofline"] = alu
     fx, rho_p, u_p = inputs.poiseuille(n, n, 0.8, 0.05)
     t = run(dict(nx=n, ny=n, tau=0.8, force=(fx, 0.0), periodic_y=False), rho_p, u_p, "f32", "dense",
             "two_lattice", 500)
