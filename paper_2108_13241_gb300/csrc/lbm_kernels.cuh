@@ -592,43 +592,6 @@ __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
     }
 }
 
-// Discrete adjoint of one node's collision (see the oracle's derivation):
-// from lam = dL/d(post-collision f) gives g = dL/df' and dL/dF.
-template <class C, bool HAS_F>
-__device__ __forceinline__ void adjoint_node(const C f[9], const C lam[9], C Fx, C Fy, C omega,
-                                             C g[9], C &dFx, C &dFy) {
-    C drho, rho, inv, ux, uy;
-    moments<C, HAS_F>(f, Fx, Fy, drho, rho, inv, ux, uy);
-    const C usq = C(1.5) * (ux * ux + uy * uy);
-    const C kk = C(1) - C(0.5) * omega;
-    C Vx = C(0), Vy = C(0), a = C(0), gx = C(0), gy = C(0);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const C w = wgt<C>(i);
-        const C t = C(cx(i)) * ux + C(cy(i)) * uy;
-        const C l = lam[i];
-        a += l * (w * (C(1) + C(3) * t + C(4.5) * t * t - usq));
-        const C wr = omega * w * rho;
-        C dx = wr * (C(3 * cx(i)) + C(9) * t * C(cx(i)) - C(3) * ux);
-        C dy = wr * (C(3 * cy(i)) + C(9) * t * C(cy(i)) - C(3) * uy);
-        if (HAS_F) {
-            const C cf = C(cx(i)) * Fx + C(cy(i)) * Fy;
-            dx += kk * w * (C(-3) * Fx + C(9) * cf * C(cx(i)));
-            dy += kk * w * (C(-3) * Fy + C(9) * cf * C(cy(i)));
-        }
-        Vx += l * dx;
-        Vy += l * dy;
-        gx += l * (kk * w * (C(3) * (C(cx(i)) - ux) + C(9) * t * C(cx(i))));
-        gy += l * (kk * w * (C(3) * (C(cy(i)) - uy) + C(9) * t * C(cy(i))));
-    }
-    a *= omega;
-#pragma unroll
-    for (int j = 0; j < 9; ++j)
-        g[j] = (C(1) - omega) * lam[j] + a + ((C(cx(j)) - ux) * Vx + (C(cy(j)) - uy) * Vy) * inv;
-    dFx = C(0.5) * Vx * inv + gx;
-    dFy = C(0.5) * Vy * inv + gy;
-}
-
 // ------------------------------------------------------------- open sides
 
 // Open side `side` at boundary node (x, y) (Zou & He, for any side): the
@@ -1080,6 +1043,59 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
 }
 
 // ------------------------------------------------------------- adjoint kernel
+
+// Discrete adjoint of one node's collision (see the oracle's derivation):
+// from lam = dL/d(post-collision f) gives g = dL/df' and dL/dF.  With
+// t_i = c_i . u, the chain rule through rho = sum f' and u = (m + F/2)/rho
+// gives
+//   g_j = (1 - omega) lam_j + omega a + (c_j - u) . V / rho
+//   a   = sum_i lam_i w_i (1 + 3 t_i + 4.5 t_i^2 - 1.5 u^2)
+//   V   = sum_i lam_i [omega rho w_i (3 c_i + 9 t_i c_i - 3 u)
+//                      + (1 - omega/2) w_i (9 (c_i . F) c_i - 3 F)]
+//   dL/dF = V / (2 rho) + (1 - omega/2) sum_i lam_i w_i (3 (c_i - u) + 9 t_i c_i),
+// and every sum over i is a combination of the weighted moments of lam,
+// Lw = sum w_i lam_i, P = sum w_i lam_i c_i, M = sum w_i lam_i c_i c_i^T
+// (sum w t = P.u, sum w t^2 = u.M.u, sum w t c = M u, sum w (c.F) c = M F).
+template <class C, bool HAS_F>
+__device__ __forceinline__ void adjoint_node(const C f[9], const C lam[9], C Fx, C Fy, C omega,
+                                             C g[9], C &dFx, C &dFy) {
+    C drho, rho, inv, ux, uy;
+    moments<C, HAS_F>(f, Fx, Fy, drho, rho, inv, ux, uy);
+    const C usq = C(1.5) * (ux * ux + uy * uy);
+    const C kk = C(1) - C(0.5) * omega;
+    const C W0 = C(4.0 / 9.0), Wa = C(1.0 / 9.0), Wd = C(1.0 / 36.0);
+    const C s13 = lam[1] + lam[3], s24 = lam[2] + lam[4], s57 = lam[5] + lam[7], s68 = lam[6] + lam[8];
+    const C d13 = lam[1] - lam[3], d24 = lam[2] - lam[4], d57 = lam[5] - lam[7], d86 = lam[8] - lam[6];
+    const C sd = s57 + s68;
+    const C Lw = W0 * lam[0] + Wa * (s13 + s24) + Wd * sd;
+    const C Px = Wa * d13 + Wd * (d57 + d86);
+    const C Py = Wa * d24 + Wd * (d57 - d86);
+    const C Mxx = Wa * s13 + Wd * sd, Myy = Wa * s24 + Wd * sd, Mxy = Wd * (s57 - s68);
+    const C Mux = Mxx * ux + Mxy * uy, Muy = Mxy * ux + Myy * uy;
+    const C a = omega * (Lw * (C(1) - usq) + C(3) * (Px * ux + Py * uy) + C(4.5) * (ux * Mux + uy * Muy));
+    const C wr = omega * rho;
+    C Vx = wr * (C(3) * (Px - ux * Lw) + C(9) * Mux);
+    C Vy = wr * (C(3) * (Py - uy * Lw) + C(9) * Muy);
+    if (HAS_F) {
+        const C MFx = Mxx * Fx + Mxy * Fy, MFy = Mxy * Fx + Myy * Fy;
+        Vx += kk * (C(9) * MFx - C(3) * Fx * Lw);
+        Vy += kk * (C(9) * MFy - C(3) * Fy * Lw);
+    }
+    const C vx = Vx * inv, vy = Vy * inv;
+    const C base = a - (ux * vx + uy * vy);
+    const C om1 = C(1) - omega;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        C e = base;
+        if (cx(j) == 1) e += vx;
+        if (cx(j) == -1) e -= vx;
+        if (cy(j) == 1) e += vy;
+        if (cy(j) == -1) e -= vy;
+        g[j] = om1 * lam[j] + e;
+    }
+    dFx = C(0.5) * vx + kk * (C(3) * (Px - ux * Lw) + C(9) * Mux);
+    dFy = C(0.5) * vy + kk * (C(3) * (Py - uy * Lw) + C(9) * Muy);
+}
 
 // Transpose of the open-side rules at node (x, y) applied to g: the rules are
 // affine in the gathered f', so their linear part is M[:, j] = R(e_j) - R(0)

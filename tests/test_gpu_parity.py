@@ -335,3 +335,22 @@ def test_low_porosity_vector_list_bitwise_equals_dense(L, precision):
             ref = g["f"]
         else:
             assert np.array_equal(g["f"], ref), (precision, layout, pattern)
+
+
+# ------------------------------------------------- the porous-medium workload
+
+@pytest.mark.parametrize("phi", [0.2, 0.5, 0.8])
+@pytest.mark.parametrize("pattern", ["two_lattice", "aa"])
+def test_porous_workload_512_matches_oracle_200_steps(L, orc, phi, pattern):
+    """The benchmark's porous medium at 512^2 with its own generator
+    parameters (seeded non-overlapping discs r in [8, 32], force (1e-6, 0),
+    periodic x, walls y, tau 0.8, from rest), tiled layout, 200 steps: FP64
+    distributions within 1e-12 of the oracle, FP32 velocity within 1e-5."""
+    solid, _, _ = inputs.porous_discs(512, 512, phi, rmin=8, rmax=32)
+    case = C.Case("porous_workload512_%g" % phi, 512, 512, 0.8, px=True, py=False, force=(1e-6, 0.0), solid=solid)
+    o = oracle_cached(orc, case, 200)
+    fl = o["mask"] != 0xFF
+    g = run_gpu(L, case, 200, "f64", "sparse", pattern)
+    assert C.rel_l2(g["f"], o["f"], fl) <= 1e-12
+    g32 = run_gpu(L, case, 200, "f32", "sparse", pattern)
+    assert C.rel_l2(g32["u"], o["u"], fl) <= 1e-5
