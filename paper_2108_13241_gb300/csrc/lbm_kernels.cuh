@@ -693,7 +693,10 @@ __device__ __forceinline__ void gather_raw(const A &ad, const typename S::R *src
     // Neighbour lanes whose VEC nodes are all solid (inactive) load nothing.
     // The values this lane pulls through them are then either solid (links
     // along x: bounced) or in the row above/below (diagonals), which this
-    // lane loads itself unless its own mask bounces that link.
+    // lane loads itself unless its own mask bounces that link.  Over the
+    // list the edge values are loaded whether bounced or not (the addresses
+    // are in bounds, the bounce-back overwrites them), so that no load of
+    // the gather waits for the mask.
     const bool lact = __shfl_up_sync(LBM_FULL, active ? 1 : 0, 1) != 0;
     const bool ract = __shfl_down_sync(LBM_FULL, active ? 1 : 0, 1) != 0;
     const bool lin = ad.left_in_warp(lane) && lact;
@@ -702,12 +705,12 @@ __device__ __forceinline__ void gather_raw(const A &ad, const typename S::R *src
     for (int i = 1; i < 9; ++i) {
         const int slot = (MODE == MODE_AA_PULLPUSH) ? opp(i) : i;
         if (cx(i) == 1) {
-            const bool bounced = (mv >> (i - 1)) & 1ull; // node 0
+            const bool bounced = !A::LIST_ && ((mv >> (i - 1)) & 1ull); // node 0
             if (active && !lin && !(ad.left_in_warp(lane) && cy(i) == 0) && !bounced)
                 edge[i] = ld1<NC>(src + ad.eidx(slot, 0, -1, -cy(i)));
         }
         if (cx(i) == -1) {
-            const bool bounced = (mv >> (8 * (VEC - 1) + i - 1)) & 1ull; // node VEC-1
+            const bool bounced = !A::LIST_ && ((mv >> (8 * (VEC - 1) + i - 1)) & 1ull); // node VEC-1
             if (active && !rin && !(ad.right_in_warp(lane) && cy(i) == 0) && !bounced)
                 edge[i] = ld1<NC>(src + ad.eidx(slot, VEC - 1, 1, -cy(i)));
         }
@@ -974,10 +977,17 @@ __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const 
     constexpr int VEC = S::VEC;
     const R *src = reinterpret_cast<const R *>(src_v);
     R *dst = reinterpret_cast<R *>(dst_v);
+    // graph replays: the step index's base, loaded first so that its latency
+    // hides behind the gather
+    unsigned tbase = 0u;
+    if constexpr (S::STOCHASTIC)
+        if (ph.tbase) tbase = (unsigned)__ldg(ph.tbase);
 
     unsigned long long mv = 0;
     if (HAS_MASK) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
-    const bool active = ad.valid && !(HAS_MASK && mv == mask_ones<VEC>());
+    // every vector of the list holds fluid: there the gather need not wait
+    // for the mask to know that
+    const bool active = ad.valid && (A::LIST_ || !(HAS_MASK && mv == mask_ones<VEC>()));
     if (!__any_sync(LBM_FULL, active)) return; // whole warp solid: no traffic
 
     V16<R, VEC> raw[9];
@@ -995,8 +1005,7 @@ __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const 
     V16<R, VEC> out[9];
     SrState sr;
     if constexpr (S::STOCHASTIC) {
-        const unsigned t = ph.tbase ? (unsigned)__ldg(ph.tbase) + step : step;
-        sr.tseed = fmix32(t * 0x9E3779B9u + 0x632BE5ABu);
+        sr.tseed = fmix32((tbase + step) * 0x9E3779B9u + 0x632BE5ABu);
     } else {
         sr.tseed = 0u;
     }
