@@ -117,10 +117,11 @@ __device__ __forceinline__ unsigned fmix32(unsigned h) {
 }
 __device__ __forceinline__ unsigned lcg_next(unsigned h) { return h * 1664525u + 1013904223u; }
 
-// One aligned vector of VEC stored values: 16 bytes (FP64, FP32) or 8 bytes
-// (FP16s), moved with one load or store instruction.
+// One aligned vector of VEC stored values: 16 bytes (FP64, FP32), 8 or 4
+// bytes (FP16s), moved with one load or store instruction.
 template <int BYTES> struct VecWord;
 template <> struct VecWord<16> { typedef uint4 T; static __device__ __forceinline__ uint4 zero() { return make_uint4(0, 0, 0, 0); } };
+template <> struct VecWord<4> { typedef unsigned T; static __device__ __forceinline__ unsigned zero() { return 0u; } };
 template <> struct VecWord<8> { typedef uint2 T; static __device__ __forceinline__ uint2 zero() { return make_uint2(0, 0); } };
 
 // The same storage with a different number of nodes per thread.
@@ -131,10 +132,16 @@ template <int P, int V> struct StV : St<P> {
 // (FP16s) vector.  FP32 with a link mask moves 2 nodes (8-byte vectors), so
 // that the preloaded bounce-back state fits 4 blocks per SM, in the AA steps,
 // with a per-node force field and in the adjoint; its two-lattice step
-// without a force field moves 4 (bounced values loaded on demand).
-template <int P, bool HAS_MASK, int MODE = MODE_AA_PULLPUSH, int FORCE = FORCE_NONE> struct StepVec {
+// without a force field moves 4 (bounced values loaded on demand).  FP16s
+// with a link mask moves 2 nodes (4-byte vectors) in the AA gather/scatter
+// step, whose scattered stores otherwise spill at 3 blocks per SM (measured
+// +14-24% on tiled and porous AA runs at 4 blocks per SM).
+template <int P, bool HAS_MASK, int MODE, int FORCE> struct StepVec {
     enum {
-        value = (P == LBM_F32 && HAS_MASK && (MODE == MODE_AA_PULLPUSH || FORCE == FORCE_FIELD)) ? 2 : St<P>::VEC
+        value = ((P == LBM_F32 && HAS_MASK && (MODE == MODE_AA_PULLPUSH || FORCE == FORCE_FIELD)) ||
+                 (P == LBM_F16S && HAS_MASK && MODE == MODE_AA_PULLPUSH))
+                    ? 2
+                    : St<P>::VEC
     };
 };
 // Whether the step preloads the own-node vectors its bounced links read
@@ -173,7 +180,8 @@ template <class R, int VEC> __device__ __forceinline__ void st16(R *p, const V16
 template <class R, int VEC> __device__ __forceinline__ void zero16(V16<R, VEC> &v) {
     v.u = VecWord<(int)sizeof(R) * VEC>::zero();
 }
-// 32-bit word W of an 8- or 16-byte vector
+// 32-bit word W of a 4-, 8- or 16-byte vector
+template <int W> __device__ __forceinline__ void set_word(unsigned &u, unsigned v) { u = v; }
 template <int W> __device__ __forceinline__ void set_word(uint2 &u, unsigned v) {
     if (W == 0) u.x = v;
     else u.y = v;
@@ -960,10 +968,14 @@ __device__ __forceinline__ void store_all(const A &ad, typename S::R *dst, unsig
 // Blocks of 256 threads each SM must hold (the register cap that follows):
 // the FP32 / FP16s step is memory-latency bound, so occupancy is fixed here
 // rather than left to the register allocator -- 4 blocks (<= 64 registers)
-// without a mask and for FP32 with a mask (2 nodes per thread), 3 blocks
-// (<= 80) for FP16s with a mask.  FP64 is ALU-bound and left free.
-template <int P, bool HAS_MASK> struct MinBlocks {
-    enum { value = P == LBM_F64 ? 1 : ((HAS_MASK && P == LBM_F16S) ? 3 : 4) };
+// without a mask, for FP32 with a mask (2 nodes per thread) and for the
+// FP16s AA gather/scatter step with a mask (2 nodes per thread), 3 blocks
+// (<= 80) for the other FP16s steps with a mask.  FP64 is ALU-bound and
+// left free.
+template <int P, bool HAS_MASK, int MODE> struct MinBlocks {
+    enum {
+        value = P == LBM_F64 ? 1 : ((HAS_MASK && P == LBM_F16S && MODE != MODE_AA_PULLPUSH) ? 3 : 4)
+    };
 };
 
 // One step of the thread's VEC nodes at address ad (every lane of the warp
@@ -1028,7 +1040,7 @@ template <int P, class A> struct ListPersist {
 // so that the list read -- the first of the three dependent loads (entry,
 // tile record, data) -- is off the critical path.
 template <int P, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN>
-__global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK>::value)
+__global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK, MODE>::value)
     k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0, int ystride, unsigned step) {
     const int lane = threadIdx.x & 31;
     if constexpr (ListPersist<P, A>::value) {
@@ -1146,7 +1158,7 @@ template <int P, int FORCE, bool OPEN>
 __global__ void __launch_bounds__(STEP_BLOCK) k_adjoint(const Geo g, const Phys ph, const void *state_v,
                                                         const void *lam_in_v, void *lam_out_v, void *gF_v,
                                                         int y0) {
-    typedef StV<P, StepVec<P, true>::value> S; // FP32: 2 nodes per thread
+    typedef StV<P, StepVec<P, true, MODE_TWO_LATTICE, FORCE_FIELD>::value> S; // FP32: 2 nodes per thread
     typedef typename S::R R;
     typedef typename S::C C;
     constexpr int VEC = S::VEC;
@@ -1717,7 +1729,7 @@ static void adjoint_open(const Geo &g, const Phys &ph, const void *state, const 
 template <int P>
 cudaError_t launch_adjoint(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
                            void *grad_force, cudaStream_t s) {
-    const Shape sh = step_shape<StepVec<P, true>::value>(g); // dense, as k_adjoint
+    const Shape sh = step_shape<StepVec<P, true, MODE_TWO_LATTICE, FORCE_FIELD>::value>(g); // dense, as k_adjoint
     if (sh.gx == 0) return cudaSuccess;
     switch (ph.force_mode) {
     case FORCE_NONE: adjoint_open<P, FORCE_NONE>(g, ph, state, lam_in, lam_out, grad_force, sh, s); break;
