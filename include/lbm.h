@@ -172,7 +172,11 @@ lbm_status lbm_step(lbm_ctx *ctx, int n);
 /* Whether lbm_step, lbm_forward_states and lbm_backward replay CUDA graphs
  * (enable != 0, the default) or issue every kernel launch from the host.
  * Launch-bound runs (small grids) gain from the graphs; a context whose
- * graph could not be recorded switches to direct launches by itself. */
+ * graph could not be recorded switches to direct launches by itself.
+ * Replacing a recorded graph (new pointers, another run length, or after
+ * lbm_set_force / lbm_set_side_values) synchronises the context's stream
+ * first, since the old graph may still be running; so does lbm_destroy of a
+ * context that recorded graphs. */
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
 
 /* Density and velocity of the current state (Eq. 2 on the gathered f'
