@@ -137,7 +137,8 @@ lbm_status lbm_workspace_bytes(const lbm_params *p, size_t *bytes);
  * initialisation).  Synchronises the stream.  *out is NULL on error. */
 lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_ctx **out);
 
-/* Frees the host context.  The workspace stays the caller's. */
+/* Frees the host context and its recorded CUDA graphs (synchronising the
+ * stream first when there are any).  The workspace stays the caller's. */
 lbm_status lbm_destroy(lbm_ctx *ctx);
 
 /* Per-node values of open side `side` (0 west, 1 east, 2 south, 3 north),
