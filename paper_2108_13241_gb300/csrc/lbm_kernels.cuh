@@ -997,8 +997,9 @@ __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const 
 
     unsigned long long mv = 0;
     if (HAS_MASK) mv = ad.valid ? ld_mask<VEC>(ad.mask_ptr()) : mask_ones<VEC>();
-    // every vector of the list holds fluid: there the gather need not wait
-    // for the mask to know that
+    // every vector of the list lies in a DRAM sector that holds fluid and is
+    // written whole (its solid nodes hold 0 and get 0): there the gather
+    // need not wait for the mask
     const bool active = ad.valid && (A::LIST_ || !(HAS_MASK && mv == mask_ones<VEC>()));
     if (!__any_sync(LBM_FULL, active)) return; // whole warp solid: no traffic
 
