@@ -9,10 +9,11 @@
 //     gather/scatter step moves it to PH_STREAMED (slot i of x holds the
 //     pulled f'_i(x) of the next step); a local step moves it back.
 //
-// Launch-bound runs (small grids: a step's kernel takes about as long as the
-// host needs to issue it) replay recorded CUDA graphs: lbm_step in chunks of
-// GRAPH_CHUNK steps, lbm_forward_states and lbm_backward as a whole once they
-// are GRAPH_MIN steps or longer.  A graph is recorded once and replayed while
+// Runs of steps replay recorded CUDA graphs, which removes the host's launch
+// cost (the bound on small grids, where a step's kernel takes about as long
+// as the host needs to issue it) and the gaps between launches: lbm_step in
+// chunks of GRAPH_CHUNK steps, lbm_forward_states and lbm_backward as a whole
+// once they are GRAPH_MIN steps or longer.  A graph is recorded once and replayed while
 // the pointers and physics it was recorded with stay the same (the autograd
 // segments reuse their state buffers, so every full segment replays); the
 // FP16s steps of a graph read their time-step index from a device counter.
