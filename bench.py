@@ -175,6 +175,74 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml) at chosen moments: the bench reads them right after the
+    timed steps are launched and again before it waits for them, so that a
+    timed region shorter than the nvidia-smi sampling period still has
+    clock samples taken under load."""
+
+    # nvmlClocksEventReasons bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, device_index: int):
+        import ctypes
+        self.rows = []
+        self.ok = False
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            handle = ctypes.c_void_p()
+            rc = -1
+            try:
+                import torch
+                p = torch.cuda.get_device_properties(device_index)
+                bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+                rc = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(handle))
+            except (AttributeError, RuntimeError):
+                rc = -1
+            if rc != 0:
+                rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index), ctypes.byref(handle))
+            if rc != 0:
+                return
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            self.lib, self.handle, self.ct = lib, handle, ctypes
+            self.ok = True
+        except (OSError, AttributeError):
+            self.ok = False
+
+    def sample(self):
+        if not self.ok:
+            return
+        ct = self.ct
+        sm, mx, rs = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+        if (self.lib.nvmlDeviceGetClockInfo(self.handle, 1, ct.byref(sm)) == 0 and
+                self.lib.nvmlDeviceGetMaxClockInfo(self.handle, 1, ct.byref(mx)) == 0 and
+                self.reasons_fn(self.handle, ct.byref(rs)) == 0):
+            self.rows.append((float(sm.value), float(mx.value),
+                              [nm for bit, nm in self.REASONS.items() if rs.value & bit]))
+
+
+def merge_clocks(smi: dict, point: "NvmlClocks"):
+    """The nvidia-smi sampler's summary joined with the NVML point samples."""
+    if not point.rows:
+        return smi
+    sms = [r[0] for r in point.rows]
+    reasons = set(r for row in point.rows for r in row[2])
+    out = dict(smi)
+    if smi.get("sm_mhz") is None:
+        out["sm_mhz"] = statistics.median(sms)
+        out["sm_max_mhz"] = max(r[1] for r in point.rows)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = 0
+    else:
+        out["reasons"] = sorted(set(smi.get("reasons", [])) | reasons)
+    out["nvml_samples_in_timed_region"] = [r[0] for r in point.rows]
+    return out
+
+
 # ---------------------------------------------------------------- workloads
 
 def build_case(workload: str, n: int, precision: str):
@@ -196,6 +264,16 @@ def build_case(workload: str, n: int, precision: str):
         nf = int((solid == 0).sum())
         return kw, None, None, nf, "porous_phi%.2f_%d" % (achieved, n)
     raise ValueError(workload)
+
+
+def bench_config(args, kw, nfluid, wname, world):
+    """The workload's description, the same for both arms."""
+    return {"workload": wname, "precision": args.precision, "layout": args.layout,
+            "pattern": args.pattern, "nodes": kw["nx"] * kw["ny"], "fluid_nodes": nfluid,
+            "tau": kw["tau"], "bytes_per_node_update": node_bytes(args.precision),
+            "parallelism": "replicas x%d" % world,
+            "l2": "working set %.0f MB > 129 MB L2, no flush needed" %
+                  (2 * 9 * BYTES_PER_VALUE[args.precision] * kw["nx"] * kw["ny"] / 1e6)}
 
 
 def sector_nodes(solid: np.ndarray, precision: str) -> int:
@@ -260,20 +338,23 @@ def run_gpu_arm(args, rank, world, dist):
 
     barrier()
     sim.step(args.warmup)
+    point = NvmlClocks(dev.index)
     barrier()
     with ClockSampler(dev.index) as clk:
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
         start.record(stream)
         sim.step(args.steps)
+        point.sample()  # the steps are queued and running
         end.record(stream)
+        point.sample()
         end.synchronize()
     barrier()
     # kernels of the timed sim.step(K): K x launches per step (graph nodes
     # included), plus the step counter's set and advances when graphs replay
     step_launches = sim.step_launches(args.steps)
     t = max_over_ranks(start.elapsed_time(end) / 1e3, dist, dev)
-    clocks = clk.summary()
+    clocks = merge_clocks(clk.summary(), point)
     mass, _ = sim.reduce()
     if not np.isfinite(mass):
         raise RuntimeError("simulation diverged")
@@ -314,12 +395,7 @@ def run_gpu_arm(args, rank, world, dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"f64": "f64", "f32": "f32", "f16s": "f16 storage, f32 compute"}[args.precision],
         "data": "synthetic (seeded Taylor-Green / Poiseuille fields, seeded disc geometries)",
-        "config": {"workload": wname, "precision": args.precision, "layout": args.layout,
-                   "pattern": args.pattern, "nodes": kw["nx"] * kw["ny"], "fluid_nodes": nfluid,
-                   "tau": kw["tau"], "bytes_per_node_update": node_bytes(args.precision),
-                   "parallelism": "replicas x%d" % world,
-                   "l2": "working set %.0f MB > 129 MB L2, no flush needed" %
-                         (2 * 9 * BYTES_PER_VALUE[args.precision] * kw["nx"] * kw["ny"] / 1e6)},
+        "config": bench_config(args, kw, nfluid, wname, world),
         "roofline": roofline,
         "e2e": {"value": round(whole_job_glups(nfluid, args.steps, world, t_e2e), 3), "unit": "GLUPS",
                 "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
@@ -394,13 +470,16 @@ def run_reference_arm(args):
         A, B = B, A
     dt = time.perf_counter() - t0
     v = S * S * args.steps / dt / 1e9
+    kw, _, _, nfluid, wname = build_case(args.workload, args.n, args.precision)
+    ref_config = bench_config(args, kw, nfluid, wname, 1)
     sample = "FP64 oracle, %d x %d periodic Taylor-Green (sample of the %d^2 workload), %d steps" % (
         S, S, args.n, args.steps)
     return {
         "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "GLUPS", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "taylor_green_%d" % args.n, "sample": "%dx%d" % (S, S)},
+        "data": "synthetic (seeded Taylor-Green / Poiseuille fields, seeded disc geometries)",
+        "config": ref_config,
         "cpu_baseline": {"value": round(v, 5), "unit": "GLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(v, 5), "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -501,12 +580,21 @@ def extra_measurements(args):
             if layout == "sparse" and (prec, layout, pattern) in dense_geom:
                 out["porous_phi%.2f_%d/%s/%s/%s" % (achieved, n, prec, layout, pattern)]["eta_P"] = round(
                     g / dense_geom[(prec, layout, pattern)], 3)
+            if prec == "f64":
+                # the masked tiled FP64 step issues at least the dense step's
+                # FP64 instructions per node, so this ceiling is an upper bound
+                alu = fp64_alu_roofline(g, torch.cuda.get_device_properties(0).multi_processor_count)
+                if alu is not None:
+                    alu["note"] = "FP64 instructions per node of the dense step (a lower bound for this step)"
+                    out[key]["alu_roofline"] = alu
         out["porous_phi%.2f_%d/fluid_nodes" % (achieved, n)] = nf
+    # eta_P of the paper's two sparse geometries (Sec. 4.2.2) at three porosities
+    out["eta_P_sweep"] = porosity_sweep(n, 300, names=("random_r8_256", "array_8x8"), phis=(0.3, 0.5, 0.8))
     out["adjoint_channel_512x256"] = adjoint_cost()
     return out
 
 
-def porosity_sweep(n: int = 4096, steps: int = 300):
+def porosity_sweep(n: int = 4096, steps: int = 300, names=None, phis=None):
     """Sparse computational efficiency eta_P (Eq. 9) over porosity, Sec. 4.2.2's
     sweep: random discs r in [8, 256] (phi 0.1 .. 0.9), the regular 8 x 8 disc
     array (phi 0.3 .. 0.9) and the r in [8, 32] discs of the porous workload
@@ -514,7 +602,8 @@ def porosity_sweep(n: int = 4096, steps: int = 300):
     Each geometry runs in the tiled layout (only tiles with fluid stored) and
     in the dense layout with the per-node link mask (the paper's bitmask-node
     comparison); eta_P divides each by the same layout on the all-fluid box
-    with the same sides.  GLUPS count fluid nodes only."""
+    with the same sides.  GLUPS count fluid nodes only.  names / phis select
+    generators and porosities (default: all of them)."""
     import torch
     from paper_2108_13241_gb300 import inputs, lbm
     stream = torch.cuda.current_stream()
@@ -540,9 +629,11 @@ def porosity_sweep(n: int = 4096, steps: int = 300):
              lambda phi: inputs.circle_array(n, n, phi, 8)[:2]),
             ("random_r8_32", [round(0.1 * k, 1) for k in range(1, 10)],
              lambda phi: inputs.porous_discs(n, n, phi, rmin=8, rmax=32)[:2])]
-    for name, phis, gen in gens:
+    for name, gen_phis, gen in gens:
+        if names is not None and name not in names:
+            continue
         rows = []
-        for phi in phis:
+        for phi in (gen_phis if phis is None else phis):
             solid, achieved = gen(phi)
             row = {"phi": round(achieved, 4)}
             for lay in ("sparse", "dense"):

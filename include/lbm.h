@@ -268,11 +268,17 @@ lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id
  * LBM_NOALLOC_MAX_ROWS * 32 + 256 bytes (512.25 KiB) that every GPU loading
  * the library keeps until the process exits.  ny > LBM_NOALLOC_MAX_ROWS (or
  * a NULL pointer, nx or ny < 1) returns LBM_ERR_INVALID before any device
- * work.  The first call on a device looks up the scratch array's device
- * address (cudaGetSymbolAddress) and caches it per device: make that first
- * call before any stream capture.  All calls share the scratch: calls that
- * overlap on the GPU (other streams, other host threads) race.  Every call
- * overwrites the scratch it reads, so nothing carries over between calls. */
+ * work.  `stream` (NULL = the legacy default stream) and every pointer must
+ * belong to the current device; a stream of another device returns
+ * LBM_ERR_INVALID.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress) and caches it per device: make that
+ * first call before any stream capture; the cached address does not survive
+ * cudaDeviceReset.  A call clears a CUDA error that an earlier call left
+ * unreported (cudaGetLastError) before it launches, and returns LBM_ERR_CUDA
+ * if either of its two launches fails.  All calls share the scratch: calls
+ * that overlap on the GPU (other streams, other host threads) race.  Every
+ * call overwrites the scratch it reads, so nothing carries over between
+ * calls. */
 lbm_status lbm_reduce_f_noalloc(lbm_precision precision, const void *d_f, const uint8_t *d_mask, int nx, int ny,
                                 double *d_out, void *stream);
 

@@ -33,7 +33,8 @@ double *g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
 // per device (host code cannot use the symbol's host-side shadow as a device
-// pointer).
+// pointer).  The cached address belongs to the device's context at the time
+// of the first call; it does not survive cudaDeviceReset.
 cudaError_t scratch_on_current_device(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -111,9 +112,22 @@ extern "C" lbm_status lbm_reduce_f_noalloc(lbm_precision precision, const void *
     if (!d_f || !d_out || nx < 1 || ny < 1) return LBM_ERR_INVALID;
     if (ny > LBM_NOALLOC_MAX_ROWS) return LBM_ERR_INVALID; // beyond the static scratch
     if (precision != LBM_F64 && precision != LBM_F32 && precision != LBM_F16S) return LBM_ERR_INVALID;
-    double *scratch = nullptr;
-    if (scratch_on_current_device(&scratch) != cudaSuccess) return LBM_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the scratch address is the current device's: the stream must belong to
+    // that device too, or the kernels would write another GPU's scratch
+    int dev = 0, sdev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    if (sdev != dev) return LBM_ERR_INVALID;
+    double *scratch = nullptr;
+    if (scratch_on_current_device(&scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    // an error left behind by an earlier, unrelated call is not this call's
+    cudaGetLastError();
     const long long nnode = (long long)nx * ny;
     double *partial = scratch;
     double *staging = scratch + (long long)LBM_NOALLOC_MAX_ROWS * 4;
@@ -121,6 +135,7 @@ extern "C" lbm_status lbm_reduce_f_noalloc(lbm_precision precision, const void *
         k_row_sums<double><<<ny, NA_BLOCK, 0, s>>>(static_cast<const double *>(d_f), d_mask, nx, nnode, partial);
     else
         k_row_sums<float><<<ny, NA_BLOCK, 0, s>>>(static_cast<const float *>(d_f), d_mask, nx, nnode, partial);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     k_rows_total<<<1, NA_BLOCK, 0, s>>>(partial, ny, staging, d_out);
     return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -293,13 +293,41 @@ def lbm_reduce_f_noalloc(precision, f: torch.Tensor, mask: Optional[torch.Tensor
                          out: torch.Tensor, stream=None):
     """Mass and momentum of canonical f [9, ny, nx] into out (3 doubles, on the
     device) without any allocation in the library (see lbm.h); only pointers
-    are passed, nothing is allocated here either."""
+    are passed, nothing is allocated here either.  The tensors are checked
+    before any device work: a wrong dtype or a short buffer would make the
+    kernel read past its end."""
     if ny > NOALLOC_MAX_ROWS:
         raise ValueError("lbm_reduce_f_noalloc: ny = %d exceeds LBM_NOALLOC_MAX_ROWS = %d (the size of its "
                          "static scratch)" % (ny, NOALLOC_MAX_ROWS))
+    if nx < 1 or ny < 1:
+        raise ValueError("lbm_reduce_f_noalloc: nx and ny must be >= 1")
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    if stream is None and torch.cuda.is_available():
-        stream = torch.cuda.current_stream().cuda_stream
+    if prec not in STORAGE_BYTES:
+        raise ValueError("lbm_reduce_f_noalloc: unknown precision %r" % (precision,))
+    want = torch.float64 if prec == LBM_F64 else torch.float32
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def on_device(name, t):
+        if t.device != dev:
+            raise ValueError("lbm_reduce_f_noalloc: %s is on %s, not on the current device %s"
+                             % (name, t.device, dev))
+        if not t.is_contiguous():
+            raise ValueError("lbm_reduce_f_noalloc: %s must be contiguous" % name)
+
+    on_device("f", f)
+    if f.dtype != want:
+        raise ValueError("lbm_reduce_f_noalloc: f must be %s for precision %r, got %s" % (want, precision, f.dtype))
+    if f.numel() < 9 * nx * ny:
+        raise ValueError("lbm_reduce_f_noalloc: f holds %d values, needs 9*nx*ny = %d" % (f.numel(), 9 * nx * ny))
+    if mask is not None:
+        on_device("mask", mask)
+        if mask.dtype != torch.uint8 or mask.numel() < nx * ny:
+            raise ValueError("lbm_reduce_f_noalloc: mask must be uint8 with at least nx*ny entries")
+    on_device("out", out)
+    if out.dtype != torch.float64 or out.numel() < 3:
+        raise ValueError("lbm_reduce_f_noalloc: out must be float64 with at least 3 entries")
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
     _check("lbm_reduce_f_noalloc", _load().lbm_reduce_f_noalloc(prec, _ptr(f), _ptr(mask), int(nx), int(ny),
                                                                 _ptr(out), stream or None))
 
