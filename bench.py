@@ -339,14 +339,16 @@ def run_gpu_arm(args, rank, world, dist):
     barrier()
     sim.step(args.warmup)
     point = NvmlClocks(dev.index)
+    point.sample()  # the first NVML query is slow: take it outside the timed region
+    point.rows.clear()
     barrier()
     with ClockSampler(dev.index) as clk:
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
         start.record(stream)
         sim.step(args.steps)
-        point.sample()  # the steps are queued and running
-        end.record(stream)
+        end.record(stream)  # queued before the host samples, so the samples add no device time
+        point.sample()      # the steps are queued and running
         point.sample()
         end.synchronize()
     barrier()

@@ -49,7 +49,7 @@ typedef enum {
     LBM_ERR_CUDA = 2,         /* CUDA runtime error (sticky)                 */
     LBM_ERR_OOM = 3,          /* workspace smaller than lbm_workspace_bytes  */
     LBM_ERR_DIVERGED = 4,     /* a reduction met NaN/Inf                     */
-    LBM_ERR_TIMEOUT = 5,      /* reserved: no call here waits on the device  */
+    LBM_ERR_TIMEOUT = 5,      /* a kernel's bounded wait expired (sticky)    */
     LBM_ERR_UNSUPPORTED = 6   /* valid request this build does not serve     */
 } lbm_status;
 
@@ -193,7 +193,10 @@ lbm_status lbm_set_f(lbm_ctx *ctx, const void *d_f);
 /* FP64 reductions over fluid nodes of the canonical state: mass
  * sum_i A_i and momentum sum_i c_i A_i.  Deterministic (fixed-order tree,
  * no atomics).  Synchronises; LBM_ERR_DIVERGED on NaN/Inf.  Either output
- * pointer may be NULL. */
+ * pointer may be NULL.  Like lbm_loss, it also reads the context's device
+ * error word: LBM_ERR_TIMEOUT (sticky) if a step kernel's wait on its own
+ * copy pipeline gave up (after about two seconds) since the context was
+ * created. */
 lbm_status lbm_reduce(lbm_ctx *ctx, double *h_mass, double h_mom[2]);
 
 /* FP64 loss of the current state over fluid nodes, Nf = fluid-node count:

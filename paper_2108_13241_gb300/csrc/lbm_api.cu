@@ -105,7 +105,8 @@ struct Plan {
     int ntiles, ntx, nty;
     bool has_mask;
     long long nslot;
-    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_tb, off_list2, off_list4, total;
+    size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_tb, off_list2, off_list4, off_vmask,
+        off_order, total;
     size_t lat_bytes, mask_bytes;
     bool use_list;
 };
@@ -117,7 +118,37 @@ struct SparseTables {
     std::vector<uint8_t> tmask;
     std::vector<uint32_t> list2, list4;
     size_t fluid2 = 0; // 2-node vectors of the kept tiles that hold fluid
+    // per tile 4 words: bit 8 * (row % 4) + v of word row / 4 set iff 2-node
+    // vector v of that row holds a fluid node
+    std::vector<uint32_t> vmask;
+    // per tile 128 bytes: the 2-node vectors (8 * row + v) of the DRAM
+    // sectors (32 bytes of one slot) that hold a fluid node, then 0xFF
+    std::vector<uint8_t> order;
 };
+
+// The staged step's tables: per tile, which 2-node vectors hold fluid (it
+// copies only those chunks) and which it computes and stores (every vector
+// of a sector that holds fluid; esize: bytes per stored value).
+void build_vector_masks(int ntiles, const std::vector<uint8_t> &tmask, size_t esize, SparseTables &st) {
+    st.vmask.assign((size_t)ntiles * 4, 0u);
+    st.order.assign((size_t)ntiles * (TILE_N / 2), 0xFF);
+    const int vps = (int)(16 / esize); // 2-node vectors per 32-byte sector
+    for (int t = 0; t < ntiles; ++t) {
+        int n = 0;
+        for (int row = 0; row < TILE; ++row) {
+            unsigned bits = 0;
+            for (int v = 0; v < TILE / 2; ++v) {
+                const uint8_t *m = &tmask[(size_t)t * TILE_N + row * TILE + 2 * v];
+                if (m[0] != 0xFF || m[1] != 0xFF) bits |= 1u << v;
+            }
+            st.vmask[(size_t)t * 4 + row / 4] |= bits << (8 * (row % 4));
+            for (int v = 0; v < TILE / 2; ++v) {
+                const unsigned sec = ((1u << vps) - 1u) << (v / vps * vps);
+                if (bits & sec) st.order[(size_t)t * (TILE_N / 2) + n++] = (uint8_t)(row * 8 + v);
+            }
+        }
+    }
+}
 
 // The lists the tiled step can run over: the 2- and 4-node vectors of the
 // kept tiles (t * TPT + position, tile order) that hold a fluid node, or,
@@ -175,6 +206,7 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
         // two-lattice step only
         const bool sectors = p.precision == LBM_F32 && p.pattern == LBM_TWO_LATTICE;
         build_vector_lists(pl.ntiles, sp.tmask, sectors ? 8 : 0, sp);
+        build_vector_masks(pl.ntiles, sp.tmask, elem_size(p.precision), sp);
     } else {
         pl.has_mask = any;
         pl.nslot = N;
@@ -207,6 +239,10 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
     if (pl.use_list) off += align256(sp.list2.size() * 4);
     pl.off_list4 = off;
     if (pl.use_list) off += align256(sp.list4.size() * 4);
+    pl.off_vmask = off;
+    if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntiles * 16);
+    pl.off_order = off;
+    if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntiles * (TILE_N / 2));
     pl.total = off;
 }
 
@@ -407,6 +443,8 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     c->partial = reinterpret_cast<double *>(ws + pl.off_part);
     c->red_out = reinterpret_cast<double *>(ws + pl.off_out);
     c->tb = reinterpret_cast<unsigned long long *>(ws + pl.off_tb);
+    // the error word shares the counter's 256-byte region
+    unsigned *err_word = reinterpret_cast<unsigned *>(ws + pl.off_tb + 16);
     c->cur = 0;
     c->phase = p->pattern == LBM_AA ? PH_SWAPPED : PH_PLAIN;
     c->steps = 0;
@@ -433,6 +471,7 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
         g.frame_y = inner_free;
     }
     g.mask = pl.mask_bytes ? reinterpret_cast<const uint8_t *>(ws + pl.off_mask) : nullptr;
+    g.err = err_word;
 
     Phys &ph = c->phys;
     std::memset(&ph, 0, sizeof(ph));
@@ -482,6 +521,7 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     lbm_status st = LBM_OK;
     cudaStream_t s = c->stream;
     st = cuda_check(c, cudaMemsetAsync(c->lat[0], 0, pl.lat_bytes, s), "memset lattice");
+    if (!st) st = cuda_check(c, cudaMemsetAsync(ws + pl.off_tb, 0, 256, s), "memset counter");
     if (!st && p->pattern == LBM_TWO_LATTICE)
         st = cuda_check(c, cudaMemsetAsync(c->lat[1], 0, pl.lat_bytes, s), "memset lattice");
     if (!st && p->layout == LBM_DENSE && pl.mask_bytes)
@@ -512,6 +552,14 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
         if (!st && pl.use_list && !sp.list4.empty())
             st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_list4, sp.list4.data(), sp.list4.size() * 4,
                                                cudaMemcpyHostToDevice, s), "copy vector list");
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_vmask, sp.vmask.data(), sp.vmask.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy vector masks");
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_order, sp.order.data(), sp.order.size(),
+                                               cudaMemcpyHostToDevice, s), "copy vector order");
+        g.tile_vmask = reinterpret_cast<const uint4 *>(ws + pl.off_vmask);
+        g.tile_order = reinterpret_cast<const uint8_t *>(ws + pl.off_order);
         g.nbr = reinterpret_cast<const int32_t *>(ws + pl.off_nbr);
         g.tile_xy = reinterpret_cast<const int32_t *>(ws + pl.off_txy);
         g.tile_id = reinterpret_cast<const int32_t *>(ws + pl.off_tid);
@@ -647,8 +695,19 @@ static lbm_status run_reduce(lbm_ctx *ctx, int kind, const void *target, double 
     if (st) return st;
     st = cuda_check(ctx, cudaMemcpyAsync(out, ctx->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                                          ctx->stream), "reduce copy");
+    unsigned err = 0;
+    if (!st)
+        st = cuda_check(ctx, cudaMemcpyAsync(&err, ctx->geo.err, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                             ctx->stream), "error word copy");
     if (st) return st;
-    return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "reduce sync");
+    st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "reduce sync");
+    if (!st && err) {
+        // a step kernel gave up waiting on its own pipeline: its results are
+        // incomplete (sticky, like a CUDA error)
+        ctx->sticky = LBM_ERR_TIMEOUT;
+        return fail(ctx, LBM_ERR_TIMEOUT, "a step kernel's bounded wait expired");
+    }
+    return st;
 }
 
 lbm_status lbm_reduce(lbm_ctx *ctx, double *h_mass, double h_mom[2]) {

@@ -53,6 +53,14 @@ struct Geo {
     float active_frac;     // listed 2-node vectors / all vectors of kept tiles
     int nlist2, nlist4;
     const unsigned *vlist2, *vlist4;
+    // sparse: per tile, bit 8 * row + v set iff 2-node vector v of that tile
+    // row holds a fluid node (row r in 32-bit word r / 4)
+    const uint4 *tile_vmask;
+    // sparse: per tile 128 bytes, the 2-node vectors (8 * row + v) whose
+    // 32-byte DRAM sector holds a fluid node, ascending, then 0xFF
+    const uint8_t *tile_order;
+    // device error word: set when a kernel's bounded wait gave up
+    unsigned *err;
 };
 
 // Physics as the kernels see it.

@@ -1064,6 +1064,8 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK, MODE>::valu
     }
 }
 
+#include "lbm_staged.cuh"
+
 // ------------------------------------------------------------- adjoint kernel
 
 // Discrete adjoint of one node's collision (see the oracle's derivation):
@@ -1621,10 +1623,40 @@ static cudaError_t step_open(const Geo &g, const Phys &ph, const void *src, void
         if (ph.has_open) return step_launch<P, A, MODE, HM, F, true>(g, ph, src, dst, t, r, s);
     return step_launch<P, A, MODE, HM, F, false>(g, ph, src, dst, t, r, s);
 }
+// The staged tiled two-lattice step: persistent, as many blocks as the SMs
+// hold (shared memory bounds them), never more than there are tiles.
+template <int P, int F, bool OPEN>
+static cudaError_t staged_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t,
+                                 cudaStream_t s) {
+    if (g.ntiles <= 0) return cudaSuccess;
+    constexpr int smem = staged_smem_bytes<P>();
+    static const unsigned cap = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_step_staged<P, F, OPEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_step_staged<P, F, OPEN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_staged<P, F, OPEN>, STG_THREADS, smem);
+        return (unsigned)(sms > 0 && per_sm > 0 ? sms * per_sm : 1);
+    }();
+    const unsigned grid = (unsigned)g.ntiles < cap ? (unsigned)g.ntiles : cap;
+    k_step_staged<P, F, OPEN><<<grid, STG_THREADS, smem, s>>>(g, ph, src, dst, t);
+    return cudaGetLastError();
+}
+
 template <int P, bool TILED, int MODE, bool HM, int F>
 static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                             cudaStream_t s) {
     constexpr int V = StepVec<P, HM, MODE, F>::value;
+    if constexpr (TILED && MODE == MODE_TWO_LATTICE && F != FORCE_FIELD && P != LBM_F64) {
+        // porous geometries: tiles staged in shared memory (uniform or no
+        // force; FP64 is bound by its FP64 pipe and keeps the per-vector step)
+        if (staged_selected<P>(g.active_frac)) {
+            if (ph.has_open) return staged_launch<P, F, true>(g, ph, src, dst, t, s);
+            return staged_launch<P, F, false>(g, ph, src, dst, t, s);
+        }
+    }
     if constexpr (TILED) {
         // over the list, FP32 keeps 8-byte vectors with the bounce-back
         // preload in every step kind (finer vectors skip more solid nodes);
