@@ -198,7 +198,9 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
         pl.ntiles = build_tile_map(p, mask.data(), tile_id.data(), nbr.data(), txy.data());
         txy.resize((size_t)pl.ntiles);
         nbr.resize((size_t)pl.ntiles * 9);
-        pl.has_mask = true;
+        // a tiled geometry without any bounced link (all fluid, both axes
+        // periodic) runs the unmasked kernels, as the dense layout does
+        pl.has_mask = any;
         pl.nslot = (long long)pl.ntiles * TILE_N;
         sp.tmask.assign((size_t)pl.ntiles * TILE_N, 0xFF);
         if (pl.ntiles > 0) build_tile_masks(p, mask.data(), txy.data(), pl.ntiles, sp.tmask.data());

@@ -81,12 +81,15 @@ template <> struct St<LBM_F32> {
 // range (|f_i - w_i| < 2^-24) the same dither is smaller than the subnormal
 // step, so those values round toward zero more often than not (bias below
 // one subnormal step, 2^-34 in f_i - w_i).
+#ifndef LBM_F16S_SHIFT
+#define LBM_F16S_SHIFT 10
+#endif
 template <> struct St<LBM_F16S> {
     typedef unsigned short R;
     typedef float C;
-    enum { VEC = 4, STOCHASTIC = 1, SCALE = 1024 }; // 8-byte vectors: 4 nodes per thread
-    static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)) * (1.0f / 1024.0f); }
-    static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c * 1024.0f)); }
+    enum { VEC = 4, STOCHASTIC = 1, SCALE = 1 << LBM_F16S_SHIFT }; // 8-byte vectors: 4 nodes per thread
+    static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)) * (1.0f / SCALE); }
+    static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c * (float)SCALE)); }
     static __device__ __forceinline__ C dec_step(R r) { return __half2float(__ushort_as_half(r)); }
     // c with 13 random bits added below binary16's last kept mantissa bit;
     // truncating the result to binary16 rounds c stochastically
@@ -1649,7 +1652,7 @@ template <int P, bool TILED, int MODE, bool HM, int F>
 static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                             cudaStream_t s) {
     constexpr int V = StepVec<P, HM, MODE, F>::value;
-    if constexpr (TILED && MODE == MODE_TWO_LATTICE && F != FORCE_FIELD && P != LBM_F64) {
+    if constexpr (TILED && HM && MODE == MODE_TWO_LATTICE && F != FORCE_FIELD && P != LBM_F64) {
         // porous geometries: tiles staged in shared memory (uniform or no
         // force; FP64 is bound by its FP64 pipe and keeps the per-vector step)
         if (staged_selected<P>(g.active_frac)) {
@@ -1709,7 +1712,8 @@ cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src,
         if (g.has_mask) return step_mode<P, false, true>(g, ph, mode, src, dst, tt, all, s);
         return step_mode<P, false, false>(g, ph, mode, src, dst, tt, all, s);
     }
-    return step_mode<P, true, true>(g, ph, mode, src, dst, tt, all, s);
+    if (g.has_mask) return step_mode<P, true, true>(g, ph, mode, src, dst, tt, all, s);
+    return step_mode<P, true, false>(g, ph, mode, src, dst, tt, all, s);
 }
 
 static inline dim3 node_blocks(const Geo &g) {

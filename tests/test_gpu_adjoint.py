@@ -126,12 +126,13 @@ def test_force_gradient_matches_fp64_finite_differences_full_size(L):
     node, T = 2000, checkpoint every 45, loss = mean |u_T - u*|^2.
 
     FP64 central differences of the GPU's FP64 forward on 64 seeded entries
-    of dL/dF: the FP64 adjoint matches them entry by entry to 1e-6; the FP32
-    adjoint (the configuration's precision) matches them to 1e-4 relative in
-    the 2-norm over the 64 entries.  The FP32 gradient's deviation is the FP32
-    forward's own (its loss differs from FP64's by ~7e-5 after 2000 steps:
-    storage rounding in a slowly varying flow accumulates coherently), so
-    each entry is only held to 5e-4."""
+    of dL/dF: the FP64 adjoint matches them entry by entry to 1e-6 (the check
+    of the adjoint's mathematics); the FP32 adjoint (the configuration's
+    precision) matches them to 1e-4 relative in the 2-norm over the 64
+    entries (measured 1.6e-5).  The FP32 gradient's per-entry deviation is
+    the FP32 forward's own (its loss differs from FP64's by ~7e-5 after 2000
+    steps: storage rounding in a slowly varying flow accumulates coherently);
+    the worst entry measured 1.23e-4, so each entry is held to 2.5e-4."""
     lbm, ag = L
     nx, ny, T, K = 512, 256, 2000, 45
     solid, _ = inputs.channel_cylinders(nx, ny, count=12, rmin=6, rmax=12, clearance=2)
@@ -183,7 +184,7 @@ def test_force_gradient_matches_fp64_finite_differences_full_size(L):
     print("FP32 adjoint vs FP64 FD: norm-wise %.3e, worst entry %.3e" % (
         norm_err, np.max(np.abs(a32 - fd) / np.maximum(np.abs(fd), floor))))
     assert norm_err <= 1e-4, norm_err
-    assert np.max(np.abs(a32 - fd) / np.maximum(np.abs(fd), floor)) <= 5e-4
+    assert np.max(np.abs(a32 - fd) / np.maximum(np.abs(fd), floor)) <= 2.5e-4
 
 
 @pytest.mark.parametrize("layout,pattern", [("sparse", "two_lattice"), ("dense", "aa")])
