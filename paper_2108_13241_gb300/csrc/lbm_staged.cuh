@@ -400,8 +400,10 @@ __global__ void __launch_bounds__(STG_THREADS, StagedBlocks<P>::value)
             return;
         }
         const unsigned char *st = stg_smem + s * L::BYTES;
-        const unsigned v = st[L::ORDER_OFF + ent]; // the lane's 2-node vector, 0xFF: none
-        if (v != 0xFFu) {
+        // the lane's 2-node vector (8 row + v); 0xFF: none.  Any byte beyond
+        // 127 is read as none, so every index stays inside the tile.
+        const unsigned v = st[L::ORDER_OFF + ent];
+        if (v < 128u) {
             const R *sd = reinterpret_cast<const R *>(st);
             const int ly = (int)(v >> 3), lx0 = 2 * (int)(v & 7u);
             const int xy = *reinterpret_cast<const int *>(st + L::XY_OFF);
