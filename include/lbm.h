@@ -56,10 +56,11 @@ typedef enum {
 /* Storage of the distributions.  Every mode stores f_i - w_i ("shifted");
  * LBM_F64 stores and computes FP64, LBM_F32 FP32.  LBM_F16S computes in FP32
  * and stores (f_i - w_i) * 2^10 in binary16 (exact power-of-two scale;
- * |f_i - w_i| <= 64); the time step rounds it stochastically with random
- * bits that depend only on the node, the link and the step index, so runs
- * are deterministic and identical across layouts and patterns; every other
- * encode (init, set_f) rounds to nearest. */
+ * |f_i - w_i| <= 64); the time step rounds it stochastically (13 random bits
+ * added below the last kept bit, then truncation) with random bits that
+ * depend only on the node pair (x even and x + 1), the link and the step
+ * index, so runs are deterministic and identical across layouts and
+ * patterns; every other encode (init, set_f) rounds to nearest. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 } lbm_precision;
 
 /* LBM_DENSE: f[i][ny][nx].  LBM_SPARSE_TILE16: only 16x16 tiles that hold a

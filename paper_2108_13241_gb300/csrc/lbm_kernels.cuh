@@ -53,8 +53,8 @@ template <class C> __host__ __device__ constexpr C wgt(int i) {
 template <int P> struct St;
 // dec/enc convert between the stored element and f_i - w_i in the compute
 // type.  The step kernel works in units of SCALE (f_i - w_i times SCALE):
-// dec_step decodes into them (FP16s encodes from them by dither and a
-// truncating conversion); every other kernel uses dec/enc.
+// dec_step decodes into them (FP16s encodes from them by a stochastically
+// rounding conversion, put_sr); every other kernel uses dec/enc.
 template <> struct St<LBM_F64> {
     typedef double R; // stored element
     typedef double C; // compute type
@@ -74,13 +74,12 @@ template <> struct St<LBM_F32> {
 // FP16s: binary16 bits of (f_i - w_i) * 2^10.  The power-of-two scale is
 // exact; it moves the small deviations of slow flows (|f_i - w_i| down to
 // 6e-8) into binary16's normal range while keeping |f_i - w_i| up to 64
-// finite.  The time step rounds stochastically (dither): the 13 mantissa
-// bits that binary16 drops get 13 uniform random bits added before
-// truncation, so the rounding error has zero mean instead of repeating
-// itself step after step in a slowly varying flow.  Below binary16's normal
-// range (|f_i - w_i| < 2^-24) the same dither is smaller than the subnormal
-// step, so those values round toward zero more often than not (bias below
-// one subnormal step, 2^-34 in f_i - w_i).
+// finite.  The time step rounds stochastically, two values by one
+// conversion (f16x2_rs below): 13 uniform random bits are added below
+// binary16's last kept mantissa bit before truncation, so the rounding error
+// has zero mean instead of repeating itself step after step in a slowly
+// varying flow.
+// log2 of the FP16s storage scale (compile-time)
 #ifndef LBM_F16S_SHIFT
 #define LBM_F16S_SHIFT 10
 #endif
@@ -91,25 +90,26 @@ template <> struct St<LBM_F16S> {
     static __device__ __forceinline__ C dec(R r) { return __half2float(__ushort_as_half(r)) * (1.0f / SCALE); }
     static __device__ __forceinline__ R enc(C c) { return __half_as_ushort(__float2half_rn(c * (float)SCALE)); }
     static __device__ __forceinline__ C dec_step(R r) { return __half2float(__ushort_as_half(r)); }
-    // c with 13 random bits added below binary16's last kept mantissa bit;
-    // truncating the result to binary16 rounds c stochastically
-    static __device__ __forceinline__ C dither(C c, unsigned rnd) {
-        return __uint_as_float(__float_as_uint(c) + (rnd >> 19));
-    }
 };
 
-// Two values truncated to binary16 by one packed conversion: lo in the low
-// half of the word (the lower node index), hi in the high half.
-__device__ __forceinline__ unsigned f16x2_rz(float lo, float hi) {
+// Two values rounded stochastically to binary16 by one packed conversion
+// (cvt.rs, sm_100 and later): lo goes to the low half of the word (the lower
+// node index) and is rounded with random bits 12..0 of rbits, hi to the high
+// half with bits 28..16 -- each adds its 13 bits below binary16's last kept
+// mantissa bit and truncates.
+__device__ __forceinline__ unsigned f16x2_rs(float lo, float hi, unsigned rbits) {
     unsigned r;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(rbits));
     return r;
 }
 
 // Counter-based random bits for stochastic rounding: the 32-bit finaliser of
-// Appleby's MurmurHash3 applied to (node index, time step), then one
-// Numerical Recipes linear congruential step per link.  Deterministic, and
-// the same for a node, link and step in every layout and pattern.
+// Appleby's MurmurHash3 applied to (index of the even node of a node pair,
+// time step), then one Numerical Recipes linear congruential step per link;
+// the word h ^ (h >> 16) rounds the pair's two values of that link (the
+// seed is well mixed, so both 13-bit fields are uniform and independent).
+// Deterministic, and the same for a node pair, link and step in every layout
+// and pattern.
 __device__ __forceinline__ unsigned fmix32(unsigned h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -852,25 +852,29 @@ __device__ __forceinline__ void load_force(const Geo &g, const Phys &ph, const A
 }
 
 // Stochastic rounding of the thread's nodes: the per-step seed, and the
-// dithered values of the even node of a pair until its odd partner is done.
+// collided values of the even node of a pair until its odd partner is done.
 struct SrState {
     unsigned tseed;
     float pend[9];
 };
 
-// Stores node K's nine dithered FP16s values: nodes 2j and 2j+1 share a
-// 32-bit word of each slot vector and are truncated together, except in the
-// AA gather/scatter step, whose x-shifted slots are stored value by value
-// (there one conversion per value measured faster).
-template <class S, int MODE, int K>
-__device__ __forceinline__ void put_sr(const float d[9], SrState &sr, V16<typename S::R, S::VEC> out[9]) {
-    constexpr bool PAIRS = MODE != MODE_AA_PULLPUSH;
+// Stores node K's nine collided FP16s values (units of the stored scale):
+// nodes 2j and 2j+1 share a 32-bit word of each slot vector and are rounded
+// together, with the pair's random stream (pair_node: index of node 2j).
+template <class S, int K>
+__device__ __forceinline__ void put_sr(const float d[9], SrState &sr, long long pair_node,
+                                       V16<typename S::R, S::VEC> out[9]) {
+    static_assert(S::VEC % 2 == 0, "FP16s vectors hold whole node pairs");
+    if constexpr ((K & 1) == 0) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        if constexpr (!PAIRS) out[i].v[K] = __half_as_ushort(__float2half_rz(d[i]));
-        else if constexpr ((K & 1) == 0 && K + 1 < S::VEC) sr.pend[i] = d[i];
-        else if constexpr ((K & 1) == 1) set_word<K / 2>(out[i].u, f16x2_rz(sr.pend[i], d[i]));
-        else out[i].v[K] = __half_as_ushort(__float2half_rz(d[i]));
+        for (int i = 0; i < 9; ++i) sr.pend[i] = d[i];
+    } else {
+        unsigned h = fmix32((unsigned)pair_node ^ sr.tseed);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            h = lcg_next(h);
+            set_word<K / 2>(out[i].u, f16x2_rs(sr.pend[i], d[i], h ^ (h >> 16)));
+        }
     }
 }
 
@@ -888,7 +892,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
     if (HAS_MASK && m == 0xFFu) {
         if constexpr (S::STOCHASTIC) {
             const float z[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            put_sr<S, MODE, K>(z, sr, out);
+            put_sr<S, K>(z, sr, ad.node(K & ~1), out);
         } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(C(0));
@@ -899,13 +903,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
     if constexpr (OPEN) apply_open<C, S::SCALE>(g, ph, ad.gx(K), ad.gy(), m, f);
     collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE>(f, Fx[K], Fy[K], co);
     if constexpr (S::STOCHASTIC) {
-        unsigned h = fmix32((unsigned)ad.node(K) ^ sr.tseed);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            h = lcg_next(h);
-            f[i] = S::dither(f[i], h);
-        }
-        put_sr<S, MODE, K>(f, sr, out);
+        put_sr<S, K>(f, sr, ad.node(K & ~1), out);
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);

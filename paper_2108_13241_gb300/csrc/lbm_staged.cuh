@@ -262,7 +262,7 @@ __device__ __forceinline__ void staged_node(const Geo &g, const Phys &ph, const 
     if (m == 0xFFu) {
         if constexpr (S::STOCHASTIC) {
             const float z[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            put_sr<S, MODE_TWO_LATTICE, K>(z, sr, out);
+            put_sr<S, K>(z, sr, (long long)gy * g.nx + gx0, out);
         } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(C(0));
@@ -288,13 +288,7 @@ __device__ __forceinline__ void staged_node(const Geo &g, const Phys &ph, const 
     const C Fx = PC<C>::fx(ph), Fy = PC<C>::fy(ph);
     collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE>(f, Fx, Fy, co);
     if constexpr (S::STOCHASTIC) {
-        unsigned h = fmix32((unsigned)((long long)gy * g.nx + gx0 + K) ^ sr.tseed);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            h = lcg_next(h);
-            f[i] = S::dither(f[i], h);
-        }
-        put_sr<S, MODE_TWO_LATTICE, K>(f, sr, out);
+        put_sr<S, K>(f, sr, (long long)gy * g.nx + gx0, out);
     } else {
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i].v[K] = S::enc(f[i]);

@@ -1,7 +1,8 @@
 """FP16-shifted storage: properties of its rounding that hold at any size.
 
 The time step stores (f_i - w_i) * 2^10 in binary16 with stochastic rounding
-(13 random bits added below the kept mantissa before truncation), so the
+(13 random bits added below the kept mantissa before truncation, two values
+per conversion instruction), so the
 storage error has zero mean, and the collision's odd part carries its
 constant as a float pair: a uniform flow, a fixed point of the update, keeps
 the mean momentum of its initial state up to zero-mean noise.  The rounding
