@@ -105,6 +105,19 @@ typedef struct {
     double rho;      /* density of a pressure side */
 } lbm_side;
 
+/* Collision operator.  LBM_BGK: the single-relaxation-time operator of
+ * Eq. 3-4, omega = 1/tau.  LBM_TRT: the two-relaxation-time operator
+ * (Ginzburg), a collision model beyond BGK of the kind the paper leaves to
+ * future work (Sec. 5): with g^+/- = (g_i +/- g_opp(i))/2,
+ *   f_i <- f_i - omega (f^+ - f^eq+) - omega_m (f^- - f^eq-)
+ *          + (1 - omega/2) G^+ + (1 - omega_m/2) G^-,
+ * G_i the Guo term w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F; the even rate
+ * omega = 1/tau sets the viscosity, the odd rate omega_m follows from the
+ * magic parameter Lambda = (1/omega - 1/2)(1/omega_m - 1/2).  Lambda = 3/16
+ * puts half-way bounce-back walls exactly half-way for channel flow at any
+ * tau; Lambda = (tau - 1/2)^2 gives BGK again. */
+typedef enum { LBM_BGK = 0, LBM_TRT = 1 } lbm_collision;
+
 typedef struct {
     int nx, ny;               /* nx % 16 == 0; LBM_SPARSE_TILE16 with a
                                  periodic y axis also needs ny % 16 == 0;
@@ -121,6 +134,8 @@ typedef struct {
     lbm_layout layout;
     lbm_pattern pattern;
     void *stream;             /* cudaStream_t, NULL = legacy default stream */
+    lbm_collision collision;  /* LBM_BGK (0) or LBM_TRT                     */
+    double magic;             /* LBM_TRT: Lambda > 0; 0 = 3/16             */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -228,7 +243,7 @@ lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long l
  * d_lambda_tmp: same size, scratch.  d_grad_force [2][ny][nx] compute type,
  * accumulated (+=): dL/dF(x) for the per-node force (the uniform force's
  * gradient is its node sum).  Entries of solid nodes come out 0.
- * LBM_ERR_UNSUPPORTED unless dense and two-lattice.  Runs of 8 steps or
+ * LBM_ERR_UNSUPPORTED unless dense, two-lattice and BGK.  Runs of 8 steps or
  * more replay a CUDA graph, recorded again when n or a pointer changes. */
 lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n,
                         void *d_lambda, void *d_lambda_tmp, void *d_grad_force);
@@ -236,7 +251,7 @@ lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n,
 /* Transpose of lbm_macros at the current state: from dL/drho [ny][nx] and
  * dL/du [2][ny][nx] (compute type, either NULL = 0) writes
  * d_lambda = dL/dA_t [9][ny][nx] and accumulates dL/dF into d_grad_force
- * (+=, may be NULL).  Dense two-lattice only. */
+ * (+=, may be NULL).  Dense two-lattice BGK only. */
 lbm_status lbm_macros_backward(lbm_ctx *ctx, const void *d_grad_rho, const void *d_grad_u,
                                void *d_lambda, void *d_grad_force);
 

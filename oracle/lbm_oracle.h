@@ -46,6 +46,10 @@ typedef struct {
     int open_kind[4];
     double open_ux[4], open_uy[4], open_rho[4];
     const double *open_val[4];
+    /* Collision operator: 0 = BGK (Eq. 4); > 0 = the two-relaxation-time
+     * (TRT) operator, whose odd parts relax at this rate while the even
+     * parts relax at 1/tau (step_body.inc). */
+    double omega_m;
 } orc_params;
 
 /* Per-node link mask value of a node that takes no part in the update. */

@@ -64,6 +64,7 @@ class Params(ctypes.Structure):
         ("open_ux", ctypes.c_double * 4), ("open_uy", ctypes.c_double * 4),
         ("open_rho", ctypes.c_double * 4),
         ("open_val", ctypes.c_void_p * 4),
+        ("omega_m", ctypes.c_double),
     ]
 
 OPEN_NONE, OPEN_VELOCITY, OPEN_PRESSURE = 0, 1, 2
@@ -85,6 +86,15 @@ class Setup:
     # the value may also be a per-node array along the side (velocity
     # [2, len], pressure [len])
     open: dict = field(default_factory=dict)
+    # two-relaxation-time collision: the magic parameter
+    # Lambda = (1/omega - 1/2)(1/omega_m - 1/2) > 0 fixes the odd rate
+    # omega_m; 0 = BGK
+    trt_magic: float = 0.0
+
+    def omega_m(self) -> float:
+        if self.trt_magic <= 0:
+            return 0.0
+        return 1.0 / (0.5 + self.trt_magic / (self.tau - 0.5))
 
     def c(self) -> Params:
         p = Params()
@@ -95,6 +105,7 @@ class Setup:
         p.tau = self.tau
         p.fx, p.fy = self.force
         p.rho_w = 1.0
+        p.omega_m = self.omega_m()
         self._keep = []
         for s, (kind, val) in self.open.items():
             length = self.ny if s < 2 else self.nx
@@ -253,8 +264,14 @@ def macros(s: Setup, mask, A, force=None):
     return rho, u
 
 
+def _bgk_only(s: Setup, what: str):
+    if s.trt_magic > 0:
+        raise NotImplementedError("%s: the oracle's adjoint covers the BGK collision only" % what)
+
+
 def adjoint_step(s: Setup, mask, A, lam_next, force=None, grad_force=None):
     """dL/dA_t from dL/dA_{t+1}; grad_force (2,ny,nx) or (2,) accumulated in place."""
+    _bgk_only(s, "adjoint_step")
     A = _f64(A, (9, s.ny, s.nx))
     lam_next = _f64(lam_next, (9, s.ny, s.nx))
     force = _f64(force, (2, s.ny, s.nx))
@@ -266,6 +283,7 @@ def adjoint_step(s: Setup, mask, A, lam_next, force=None, grad_force=None):
 
 
 def macros_adjoint(s: Setup, mask, A, g_rho, g_u, force=None, lam=None, grad_force=None):
+    _bgk_only(s, "macros_adjoint")
     A = _f64(A, (9, s.ny, s.nx))
     force = _f64(force, (2, s.ny, s.nx))
     if lam is None:

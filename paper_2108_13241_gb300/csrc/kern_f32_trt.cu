@@ -1,0 +1,8 @@
+// kern_f32_trt.cu -- instantiates the step kernels with the two-relaxation-time
+// collision for LBM_F32 storage (a translation unit of its own, compiled in
+// parallel with the BGK instances of kern_f32.cu).
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+LBM_INSTANTIATE_STEP(LBM_F32, true)
+} // namespace lbm

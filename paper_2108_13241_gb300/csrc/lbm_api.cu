@@ -81,6 +81,9 @@ const char *check_params(const lbm_params *p) {
     if (p->precision < LBM_F64 || p->precision > LBM_F16S) return "unknown precision";
     if (p->layout != LBM_DENSE && p->layout != LBM_SPARSE_TILE16) return "unknown layout";
     if (p->pattern != LBM_TWO_LATTICE && p->pattern != LBM_AA) return "unknown pattern";
+    if (p->collision != LBM_BGK && p->collision != LBM_TRT) return "unknown collision";
+    if (p->collision == LBM_TRT && (!std::isfinite(p->magic) || p->magic < 0.0))
+        return "TRT magic parameter must be finite and >= 0 (0 = 3/16)";
     if (p->layout == LBM_SPARSE_TILE16 && p->south.periodic && p->ny % 16)
         return "sparse layout with a periodic y axis needs ny % 16 == 0";
     const lbm_side *s[4] = {&p->west, &p->east, &p->south, &p->north};
@@ -518,6 +521,27 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     }
     ph.tau_h = 1.0 / ph.omega - 0.5;
     ph.tau_h_f = (float)(1.0 / (double)ph.omega_f - 0.5);
+    // two-relaxation-time: odd rate from Lambda = (1/omega - 1/2)(1/omega_m - 1/2)
+    ph.trt = p->collision == LBM_TRT;
+    {
+        const double lam = p->magic > 0.0 ? p->magic : 3.0 / 16.0;
+        ph.omega_m = ph.trt ? 1.0 / (0.5 + lam / (p->tau - 0.5)) : ph.omega;
+        ph.tp = 0.5 * (1.0 - ph.omega);
+        ph.tm = 0.5 * (1.0 - ph.omega_m);
+        ph.kqm[0] = ph.omega_m / 3.0;
+        ph.kqm[1] = ph.omega_m / 12.0;
+        ph.thm = 1.0 / ph.omega_m - 0.5;
+        const float omf = (float)ph.omega_m;
+        ph.tp_f = 0.5f * ph.om1_f;   // exact: om1_f = 1 - omega_f exactly
+        ph.tm_f = 0.5f * (1.0f - omf);
+        for (int q = 0; q < 2; ++q) {
+            const double k = (double)omf / (q == 0 ? 3.0 : 12.0);
+            ph.kqm_hi[q] = (float)k;
+            ph.kqm_lo[q] = (float)(k - (double)ph.kqm_hi[q]);
+        }
+        ph.thm_f = (float)(1.0 / (double)omf - 0.5);
+        ph.kkm_f = 1.0f - 0.5f * omf;
+    }
     set_force_mode(c);
 
     lbm_status st = LBM_OK;
@@ -802,8 +826,8 @@ lbm_status lbm_forward_states(lbm_ctx *ctx, void *const *h_states, int n, long l
 lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n, void *d_lambda, void *d_lambda_tmp,
                         void *d_grad_force) {
     LBM_CTX_CHECK(ctx);
-    if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
-        return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
+    if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE || ctx->phys.trt)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice BGK configuration");
     if (n < 0 || (n > 0 && (!h_states || !d_lambda || !d_lambda_tmp || !d_grad_force)))
         return fail(ctx, LBM_ERR_INVALID, "bad backward arguments");
     if (((uintptr_t)d_lambda & 15) || ((uintptr_t)d_lambda_tmp & 15) || ((uintptr_t)d_grad_force & 15))
@@ -842,8 +866,8 @@ lbm_status lbm_backward(lbm_ctx *ctx, const void *const *h_states, int n, void *
 lbm_status lbm_macros_backward(lbm_ctx *ctx, const void *d_grad_rho, const void *d_grad_u, void *d_lambda,
                                void *d_grad_force) {
     LBM_CTX_CHECK(ctx);
-    if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE)
-        return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice configuration");
+    if (ctx->p.layout != LBM_DENSE || ctx->p.pattern != LBM_TWO_LATTICE || ctx->phys.trt)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "adjoint needs the dense two-lattice BGK configuration");
     if (!d_lambda) return fail(ctx, LBM_ERR_INVALID, "d_lambda is NULL");
     return cuda_check(ctx, LBM_DISPATCH(ctx->p.precision,
                                         launch_macros_adjoint<P>(ctx->geo, ctx->phys, ctx->lat[ctx->cur],

@@ -82,6 +82,13 @@ struct Phys {
     // the equilibrium's (FP64, and from omega_f for FP32 / FP16s)
     double tau_h;
     float tau_h_f;
+    // two-relaxation-time collision (trt != 0): the odd rate omega_m and
+    // f_i <- tp (f_i + f_opp) + tm (f_i - f_opp) + ..., tp = (1 - omega)/2,
+    // tm = (1 - omega_m)/2; odd constants omega_m/3, omega_m/12 (FP64; FP32
+    // float pair), 1/omega_m - 1/2, and 1 - omega_m/2 (FP32)
+    int trt;
+    double omega_m, tp, tm, kqm[2], thm;
+    float tp_f, tm_f, kqm_hi[2], kqm_lo[2], thm_f, kkm_f;
     // when set, the step kernel's time-step index is *tbase + its step
     // argument (steps replayed from a CUDA graph, whose arguments are fixed)
     const unsigned long long *tbase;
@@ -96,10 +103,17 @@ struct Phys {
 
 // Launchers, defined in lbm_kernels.cuh and instantiated per precision P
 // (an lbm_precision value) in kern_f64.cu, kern_f32.cu, kern_f16s.cu.
-// t: index of the time step (random bits of FP16s stochastic rounding)
-template <int P> cudaError_t launch_step(const Geo &g, const Phys &ph, int mode,
-                                         const void *src, void *dst, unsigned long long t,
-                                         cudaStream_t s);
+// t: index of the time step (random bits of FP16s stochastic rounding);
+// TRT: the two-relaxation-time collision instead of BGK (launch_step picks
+// it from ph.trt); its instances are built in kern_*_trt.cu.
+template <int P, bool TRT> cudaError_t launch_step_op(const Geo &g, const Phys &ph, int mode,
+                                                      const void *src, void *dst, unsigned long long t,
+                                                      cudaStream_t s);
+template <int P> inline cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src,
+                                                void *dst, unsigned long long t, cudaStream_t s) {
+    return ph.trt ? launch_step_op<P, true>(g, ph, mode, src, dst, t, s)
+                  : launch_step_op<P, false>(g, ph, mode, src, dst, t, s);
+}
 template <int P> cudaError_t launch_init(const Geo &g, int phase, const void *rho,
                                          const void *u, void *lat, cudaStream_t s);
 template <int P> cudaError_t launch_set_f(const Geo &g, int phase, const void *f, void *lat,

@@ -474,20 +474,131 @@ __device__ __forceinline__ void moments(const C f[9], C Fx, C Fy, C &drho, C &rh
 template <class C> struct Coef {
     C om, om1, kk, th;
     C kh[2], kl[2]; // omega/3, omega/12 (axis, diagonal); kl: low part (FP32)
+    // two-relaxation-time: tp = (1 - omega)/2, tm = (1 - omega_m)/2, the odd
+    // constants omega_m/3, omega_m/12 (float pair in FP32), 1/omega_m - 1/2,
+    // 1 - omega_m/2
+    int trt;
+    C tp, tm, khm[2], klm[2], thm, kkm;
     __device__ __forceinline__ explicit Coef(const Phys &ph)
-        : om(PC<C>::omega(ph)), om1(PC<C>::om1(ph)), kk(PC<C>::kk(ph)), th(PC<C>::tau_h(ph)) {
+        : om(PC<C>::omega(ph)), om1(PC<C>::om1(ph)), kk(PC<C>::kk(ph)), th(PC<C>::tau_h(ph)), trt(ph.trt) {
         if constexpr (sizeof(C) == 8) {
             kh[0] = C(ph.kq[0]);
             kh[1] = C(ph.kq[1]);
             kl[0] = kl[1] = C(0);
+            tp = C(ph.tp);
+            tm = C(ph.tm);
+            khm[0] = C(ph.kqm[0]);
+            khm[1] = C(ph.kqm[1]);
+            klm[0] = klm[1] = C(0);
+            thm = C(ph.thm);
+            kkm = C(1.0 - 0.5 * ph.omega_m);
         } else {
             kh[0] = C(ph.kq_hi[0]);
             kh[1] = C(ph.kq_hi[1]);
             kl[0] = C(ph.kq_lo[0]);
             kl[1] = C(ph.kq_lo[1]);
+            tp = C(ph.tp_f);
+            tm = C(ph.tm_f);
+            khm[0] = C(ph.kqm_hi[0]);
+            khm[1] = C(ph.kqm_hi[1]);
+            klm[0] = C(ph.kqm_lo[0]);
+            klm[1] = C(ph.kqm_lo[1]);
+            thm = C(ph.thm_f);
+            kkm = C(ph.kkm_f);
         }
     }
 };
+
+// Two-relaxation-time collision (Coef::trt) on the moments collide() has
+// formed: the even part of every pair of opposite links relaxes exactly as
+// in BGK at omega, the odd part at omega_m, and each part gets its share of
+// the Guo source with its own factor (1 - rate/2):
+//   f_i <- tp (f_i + f_opp) + tm (f_i - f_opp) + E_i + O_i,
+//   f_opp <- tp (f_i + f_opp) - tm (f_i - f_opp) + E_i - O_i,
+// E_i the even part of omega (f^eq_i - w_i) + (1 - omega/2) G_i (as in BGK),
+// O_i = 3 w_i omega_m (c_i . (j + (1/omega_m - 1/2) F)) its odd part, j = rho u.
+// COMP (FP32 storage): the odd constant as a float pair with an error-free
+// product, tm from 1 - omega_m exactly, as in the BGK form.
+template <class C, bool HAS_F, bool COMP, int SC>
+__device__ __forceinline__ void collide_trt(C f[9], C Fx, C Fy, const Coef<C> &co, C drho, C rs, C ux, C uy,
+                                            C jx, C jy, C jxl, C jyl, C usq, C uF) {
+    const C om = co.om, om1 = co.om1, tp = co.tp, tm = co.tm;
+    if constexpr (COMP) {
+        C K0 = C(0), Ka = C(0), Kd = C(0), Kam = C(0), Kdm = C(0);
+        if (HAS_F) {
+            K0 = co.kk * C(4.0 / 9.0);
+            Ka = co.kk * C(1.0 / 9.0);
+            Kd = co.kk * C(1.0 / 36.0);
+            Kam = co.kkm * C(1.0 / 9.0);
+            Kdm = co.kkm * C(1.0 / 36.0);
+        }
+        const C R0 = (om * C(4.0 / 9.0)) * rs, Ra = (om * C(1.0 / 9.0)) * rs, Rd = (om * C(1.0 / 36.0)) * rs;
+        const C E0 = (om * C(4.0 / 9.0)) * drho, Ea = (om * C(1.0 / 9.0)) * drho, Ed = (om * C(1.0 / 36.0)) * drho;
+        {
+            C G = E0 - R0 * usq;
+            if (HAS_F) G = G + K0 * (C(-3) * uF);
+            f[0] = om1 * f[0] + G;
+        }
+#define LBM_TRT_PAIR(I, J, T, SH, SL, CF, RQ, EQ, KQ, KQM, Q)                                 \
+    {                                                                                       \
+        const C t = (T);                                                                    \
+        C P = EQ + RQ * (C(4.5) * (t * t) - usq);                                           \
+        const C qh = rn_mul(co.khm[Q], (SH));                                               \
+        C ql = rn_add(rn_fma(co.khm[Q], (SH), -qh), rn_fma(co.khm[Q], (SL), rn_mul(co.klm[Q], (SH)))); \
+        if (HAS_F) {                                                                        \
+            const C cf = (CF);                                                              \
+            P = P + KQ * (C(9) * (t * cf) - C(3) * uF);                                     \
+            ql = ql + (C(3) * KQM) * cf;                                                    \
+        }                                                                                   \
+        const C sp = f[I] + f[J], sm = f[I] - f[J];                                         \
+        f[I] = tp * sp + tm * sm + rn_add(rn_add(P, qh), ql);                               \
+        f[J] = tp * sp - tm * sm + rn_sub(rn_sub(P, qh), ql);                               \
+    }
+        C sd1h, sd1l, sd2h, sd2l;
+        two_sum(jx, jy, sd1h, sd1l);
+        two_sum(jy, -jx, sd2h, sd2l);
+        if (HAS_F) {
+            sd1l = sd1l + (jxl + jyl);
+            sd2l = sd2l + (jyl - jxl);
+        }
+        LBM_TRT_PAIR(1, 3, ux, jx, jxl, Fx, Ra, Ea, Ka, Kam, 0)
+        LBM_TRT_PAIR(2, 4, uy, jy, jyl, Fy, Ra, Ea, Ka, Kam, 0)
+        LBM_TRT_PAIR(5, 7, ux + uy, sd1h, sd1l, Fx + Fy, Rd, Ed, Kd, Kdm, 1)
+        LBM_TRT_PAIR(6, 8, uy - ux, sd2h, sd2l, Fy - Fx, Rd, Ed, Kd, Kdm, 1)
+#undef LBM_TRT_PAIR
+    } else {
+        C Z = drho - rs * usq;
+        const C r45 = C(4.5) * rs;
+        const C w0 = om * C(4.0 / 9.0), wa = om * C(1.0 / 9.0), wd = om * C(1.0 / 36.0);
+        C vx = jx, vy = jy, kx = jx, ky = jy;
+        if (HAS_F) {
+            const C h = co.th * C(SC), hm = co.thm * C(SC);
+            Z = Z - (C(3) * h) * uF;
+            kx = jx + hm * Fx;
+            ky = jy + hm * Fy;
+            vx = jx + (C(2) * h) * Fx;
+            vy = jy + (C(2) * h) * Fy;
+        }
+        f[0] = om1 * f[0] + w0 * Z;
+#define LBM_TRT_PAIR(I, J, T, TV, SK, WQ, Q)                                                \
+    {                                                                                       \
+        const C t = (T);                                                                    \
+        C y;                                                                                \
+        if (HAS_F) y = Z + (C(4.5) * t) * (TV);                                             \
+        else y = Z + r45 * (t * t);                                                         \
+        C q = co.khm[Q] * (SK);                                                             \
+        if constexpr (sizeof(C) == 4) q = q + co.klm[Q] * (SK);                             \
+        const C e = WQ * y, sp = f[I] + f[J], sm = f[I] - f[J];                             \
+        f[I] = tp * sp + tm * sm + (e + q);                                                 \
+        f[J] = tp * sp - tm * sm + (e - q);                                                 \
+    }
+        LBM_TRT_PAIR(1, 3, ux, vx, kx, wa, 0)
+        LBM_TRT_PAIR(2, 4, uy, vy, ky, wa, 0)
+        LBM_TRT_PAIR(5, 7, ux + uy, vx + vy, kx + ky, wd, 1)
+        LBM_TRT_PAIR(6, 8, uy - ux, vy - vx, ky - kx, wd, 1)
+#undef LBM_TRT_PAIR
+    }
+}
 
 // BGK relaxation with Guo source, in shifted variables, in place on f:
 //   f_i <- f_i + omega (f^eq_i - w_i - f_i) + S_i
@@ -506,7 +617,7 @@ template <class C> struct Coef {
 // SC: f in units of SC (the FP16s step works in f - w times 2^10, so its
 // decode and encode need no scaling); the constants that multiply plain
 // quantities (rho, u, F) carry the factor.
-template <class C, bool HAS_F, bool COMP, int SC = 1>
+template <class C, bool HAS_F, bool COMP, int SC = 1, bool TRT = false>
 __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
     static_assert(SC == 1 || !COMP, "the compensated form works in plain units");
     C drho, rho, inv, ux, uy, jx, jy, jxl, jyl;
@@ -515,6 +626,10 @@ __device__ __forceinline__ void collide(C f[9], C Fx, C Fy, const Coef<C> &co) {
     const C om = co.om, om1 = co.om1;
     const C rs = rho * C(SC);
     const C uF = HAS_F ? ux * Fx + uy * Fy : C(0);
+    if constexpr (TRT) {
+        collide_trt<C, HAS_F, COMP, SC>(f, Fx, Fy, co, drho, rs, ux, uy, jx, jy, jxl, jyl, usq, uF);
+        return;
+    }
     if constexpr (COMP) {
         // Guo source weights (1 - omega/2) w_q
         C K0 = C(0), Ka = C(0), Kd = C(0);
@@ -878,7 +993,7 @@ __device__ __forceinline__ void put_sr(const float d[9], SrState &sr, long long 
     }
 }
 
-template <class S, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, int K>
+template <class S, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, int K, bool TRT>
 __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                         const V16<typename S::R, S::VEC> own[9],
                                         unsigned long long mv, const V16<typename S::R, S::VEC> raw[9],
@@ -901,7 +1016,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
     }
     if (HAS_MASK && m != 0u) bounce<S, MODE>(g, ph, ad, src, raw, own, K, m, f);
     if constexpr (OPEN) apply_open<C, S::SCALE>(g, ph, ad.gx(K), ad.gy(), m, f);
-    collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE>(f, Fx[K], Fy[K], co);
+    collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE, TRT>(f, Fx[K], Fy[K], co);
     if constexpr (S::STOCHASTIC) {
         put_sr<S, K>(f, sr, ad.node(K & ~1), out);
     } else {
@@ -911,7 +1026,7 @@ __device__ __forceinline__ void do_node(const Geo &g, const Phys &ph, const A &a
 }
 
 // Nodes K0 .. K1-1 of the thread, in order (compile-time unrolled).
-template <class S, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, int K, int K1>
+template <class S, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, int K, int K1, bool TRT>
 struct NodeRange {
     static __device__ __forceinline__ void run(const Geo &g, const Phys &ph, const A &ad, const typename S::R *src,
                                                const V16<typename S::R, S::VEC> own[9],
@@ -921,8 +1036,9 @@ struct NodeRange {
                                                const typename S::C Fy[], const Coef<typename S::C> &co,
                                                SrState &sr, V16<typename S::R, S::VEC> out[9]) {
         if constexpr (K < K1) {
-            do_node<S, A, MODE, HAS_MASK, FORCE, OPEN, K>(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr, out);
-            NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, K + 1, K1>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy,
+            do_node<S, A, MODE, HAS_MASK, FORCE, OPEN, K, TRT>(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr,
+                                                                out);
+            NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, K + 1, K1, TRT>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy,
                                                                          co, sr, out);
         }
     }
@@ -981,7 +1097,7 @@ template <int P, bool HAS_MASK, int MODE> struct MinBlocks {
 
 // One step of the thread's VEC nodes at address ad (every lane of the warp
 // enters together; the gather's shuffles are the only collective operations).
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN>
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, bool TRT>
 __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const void *src_v, void *dst_v,
                                             const A &ad, int lane, unsigned step) {
     typedef StV<P, A::VEC_> S;
@@ -1023,7 +1139,8 @@ __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const 
     } else {
         sr.tseed = 0u;
     }
-    NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, 0, VEC>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr, out);
+    NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, 0, VEC, TRT>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr,
+                                                                   out);
     store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
 }
 
@@ -1041,7 +1158,7 @@ template <int P, class A> struct ListPersist {
 // loading the entry of its next chunk before it works on the current one,
 // so that the list read -- the first of the three dependent loads (entry,
 // tile record, data) -- is off the critical path.
-template <int P, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN>
+template <int P, class A, int MODE, bool HAS_MASK, int FORCE, bool OPEN, bool TRT>
 __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK, MODE>::value)
     k_step(const Geo g, const Phys ph, const void *src_v, void *dst_v, int y0, int ystride, unsigned step) {
     const int lane = threadIdx.x & 31;
@@ -1054,14 +1171,14 @@ __global__ void __launch_bounds__(STEP_BLOCK, MinBlocks<P, HAS_MASK, MODE>::valu
             const int cn = c + nwarps;
             const unsigned en = A::entry(g, cn * 32 + lane);
             const A ad(g, e, c * 32 + lane < n);
-            step_vector<P, A, MODE, HAS_MASK, FORCE, OPEN>(g, ph, src_v, dst_v, ad, lane, step);
+            step_vector<P, A, MODE, HAS_MASK, FORCE, OPEN, TRT>(g, ph, src_v, dst_v, ad, lane, step);
             __syncwarp();
             e = en;
             c = cn;
         }
     } else {
         const A ad(g, (int)(blockIdx.x * blockDim.x + threadIdx.x), y0 + ystride * (int)blockIdx.y);
-        step_vector<P, A, MODE, HAS_MASK, FORCE, OPEN>(g, ph, src_v, dst_v, ad, lane, step);
+        step_vector<P, A, MODE, HAS_MASK, FORCE, OPEN, TRT>(g, ph, src_v, dst_v, ad, lane, step);
     }
 }
 
@@ -1590,7 +1707,7 @@ template <int VEC, bool LIST = false> static Shape step_shape(const Geo &g) {
 struct Rows {
     int row0, nrows, stride;
 };
-template <int P, class A, int MODE, bool HM, int F, bool OPEN>
+template <int P, class A, int MODE, bool HM, int F, bool OPEN, bool TRT>
 static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                                cudaStream_t s) {
     Shape sh = step_shape<A::VEC_, A::LIST_>(g);
@@ -1601,7 +1718,7 @@ static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, vo
             int dev = 0, sms = 0, per_sm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<P, A, MODE, HM, F, OPEN>, STEP_BLOCK, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<P, A, MODE, HM, F, OPEN, TRT>, STEP_BLOCK, 0);
             return (unsigned)(sms > 0 && per_sm > 0 ? sms * per_sm : 1);
         }();
         if (sh.gx > cap) sh.gx = cap;
@@ -1609,24 +1726,24 @@ static cudaError_t step_launch(const Geo &g, const Phys &ph, const void *src, vo
     const unsigned rows = sh.dense ? (unsigned)r.nrows : 1u;
     for (unsigned k = 0; k < rows; k += 65535u) {
         const unsigned gy = rows - k < 65535u ? rows - k : 65535u;
-        k_step<P, A, MODE, HM, F, OPEN><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst, r.row0 + (int)k * r.stride,
-                                                                    r.stride, t);
+        k_step<P, A, MODE, HM, F, OPEN, TRT><<<dim3(sh.gx, gy), sh.bx, 0, s>>>(g, ph, src, dst,
+                                                                         r.row0 + (int)k * r.stride, r.stride, t);
     }
     return cudaGetLastError();
 }
 // Dense (TILED false) or tiled addressing with the vector width of the step
 // kind, the force mode and the mask flag.
-template <int P, class A, int MODE, bool HM, int F>
+template <int P, class A, int MODE, bool HM, int F, bool TRT>
 static cudaError_t step_open(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                              cudaStream_t s) {
     // open sides are only on masked kernels (their links are marked)
     if constexpr (HM)
-        if (ph.has_open) return step_launch<P, A, MODE, HM, F, true>(g, ph, src, dst, t, r, s);
-    return step_launch<P, A, MODE, HM, F, false>(g, ph, src, dst, t, r, s);
+        if (ph.has_open) return step_launch<P, A, MODE, HM, F, true, TRT>(g, ph, src, dst, t, r, s);
+    return step_launch<P, A, MODE, HM, F, false, TRT>(g, ph, src, dst, t, r, s);
 }
 // The staged tiled two-lattice step: persistent, as many blocks as the SMs
 // hold (shared memory bounds them), never more than there are tiles.
-template <int P, int F, bool OPEN>
+template <int P, int F, bool OPEN, bool TRT>
 static cudaError_t staged_launch(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t,
                                  cudaStream_t s) {
     if (g.ntiles <= 0) return cudaSuccess;
@@ -1635,18 +1752,18 @@ static cudaError_t staged_launch(const Geo &g, const Phys &ph, const void *src, 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_step_staged<P, F, OPEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_step_staged<P, F, OPEN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_step_staged<P, F, OPEN, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_step_staged<P, F, OPEN, TRT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_staged<P, F, OPEN>, STG_THREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_staged<P, F, OPEN, TRT>, STG_THREADS, smem);
         return (unsigned)(sms > 0 && per_sm > 0 ? sms * per_sm : 1);
     }();
     const unsigned grid = (unsigned)g.ntiles < cap ? (unsigned)g.ntiles : cap;
-    k_step_staged<P, F, OPEN><<<grid, STG_THREADS, smem, s>>>(g, ph, src, dst, t);
+    k_step_staged<P, F, OPEN, TRT><<<grid, STG_THREADS, smem, s>>>(g, ph, src, dst, t);
     return cudaGetLastError();
 }
 
-template <int P, bool TILED, int MODE, bool HM, int F>
+template <int P, bool TILED, int MODE, bool HM, int F, bool TRT>
 static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                             cudaStream_t s) {
     constexpr int V = StepVec<P, HM, MODE, F>::value;
@@ -1654,8 +1771,8 @@ static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void 
         // porous geometries: tiles staged in shared memory (uniform or no
         // force; FP64 is bound by its FP64 pipe and keeps the per-vector step)
         if (staged_selected<P>(g.active_frac)) {
-            if (ph.has_open) return staged_launch<P, F, true>(g, ph, src, dst, t, s);
-            return staged_launch<P, F, false>(g, ph, src, dst, t, s);
+            if (ph.has_open) return staged_launch<P, F, true, TRT>(g, ph, src, dst, t, s);
+            return staged_launch<P, F, false, TRT>(g, ph, src, dst, t, s);
         }
     }
     if constexpr (TILED) {
@@ -1666,28 +1783,28 @@ static cudaError_t step_vec(const Geo &g, const Phys &ph, const void *src, void 
         constexpr int VL = P == LBM_F32 ? 2 : V;
         constexpr bool WIDE = P == LBM_F32 && MODE == MODE_TWO_LATTICE && F != FORCE_FIELD;
         if (g.use_list && g.active_frac < (WIDE ? 0.67f : 0.85f))
-            return step_open<P, TileAddr<VL, true>, MODE, HM, F>(g, ph, src, dst, t, r, s);
-        return step_open<P, TileAddr<V, false>, MODE, HM, F>(g, ph, src, dst, t, r, s);
+            return step_open<P, TileAddr<VL, true>, MODE, HM, F, TRT>(g, ph, src, dst, t, r, s);
+        return step_open<P, TileAddr<V, false>, MODE, HM, F, TRT>(g, ph, src, dst, t, r, s);
     } else {
-        return step_open<P, DenseAddr<V>, MODE, HM, F>(g, ph, src, dst, t, r, s);
+        return step_open<P, DenseAddr<V>, MODE, HM, F, TRT>(g, ph, src, dst, t, r, s);
     }
 }
-template <int P, bool TILED, int MODE, bool HM>
+template <int P, bool TILED, int MODE, bool HM, bool TRT>
 static cudaError_t step_force(const Geo &g, const Phys &ph, const void *src, void *dst, unsigned t, Rows r,
                               cudaStream_t s) {
     switch (ph.force_mode) {
-    case FORCE_NONE: return step_vec<P, TILED, MODE, HM, FORCE_NONE>(g, ph, src, dst, t, r, s);
-    case FORCE_UNIFORM: return step_vec<P, TILED, MODE, HM, FORCE_UNIFORM>(g, ph, src, dst, t, r, s);
-    default: return step_vec<P, TILED, MODE, HM, FORCE_FIELD>(g, ph, src, dst, t, r, s);
+    case FORCE_NONE: return step_vec<P, TILED, MODE, HM, FORCE_NONE, TRT>(g, ph, src, dst, t, r, s);
+    case FORCE_UNIFORM: return step_vec<P, TILED, MODE, HM, FORCE_UNIFORM, TRT>(g, ph, src, dst, t, r, s);
+    default: return step_vec<P, TILED, MODE, HM, FORCE_FIELD, TRT>(g, ph, src, dst, t, r, s);
     }
 }
-template <int P, bool TILED, bool HM>
+template <int P, bool TILED, bool HM, bool TRT>
 static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned t, Rows r,
                              cudaStream_t s) {
     switch (mode) {
-    case MODE_TWO_LATTICE: return step_force<P, TILED, MODE_TWO_LATTICE, HM>(g, ph, src, dst, t, r, s);
-    case MODE_AA_PULLPUSH: return step_force<P, TILED, MODE_AA_PULLPUSH, HM>(g, ph, src, dst, t, r, s);
-    default: return step_force<P, TILED, MODE_AA_LOCAL, HM>(g, ph, src, dst, t, r, s);
+    case MODE_TWO_LATTICE: return step_force<P, TILED, MODE_TWO_LATTICE, HM, TRT>(g, ph, src, dst, t, r, s);
+    case MODE_AA_PULLPUSH: return step_force<P, TILED, MODE_AA_PULLPUSH, HM, TRT>(g, ph, src, dst, t, r, s);
+    default: return step_force<P, TILED, MODE_AA_LOCAL, HM, TRT>(g, ph, src, dst, t, r, s);
     }
 }
 
@@ -1695,23 +1812,25 @@ static cudaError_t step_mode(const Geo &g, const Phys &ph, int mode, const void 
 // or open sides in y, periodic x, no obstacle): those two rows run the
 // masked kernel, every other row the kernel without a mask.  Both read the
 // state before the step and write disjoint nodes (two-lattice), or touch
-// disjoint slot sets (AA), so the split is exact.
-template <int P>
-cudaError_t launch_step(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned long long t,
-                        cudaStream_t s) {
+// disjoint slot sets (AA), so the split is exact.  TRT: the
+// two-relaxation-time collision (its kernels are separate instances, built
+// in their own translation units).
+template <int P, bool TRT>
+cudaError_t launch_step_op(const Geo &g, const Phys &ph, int mode, const void *src, void *dst, unsigned long long t,
+                           cudaStream_t s) {
     const unsigned tt = (unsigned)t;
     const Rows all = {0, g.ny, 1};
     if (g.layout == LBM_DENSE) {
         if (g.has_mask && g.frame_y) {
-            cudaError_t e = step_mode<P, false, true>(g, ph, mode, src, dst, tt, Rows{0, 2, g.ny - 1}, s);
+            cudaError_t e = step_mode<P, false, true, TRT>(g, ph, mode, src, dst, tt, Rows{0, 2, g.ny - 1}, s);
             if (e != cudaSuccess) return e;
-            return step_mode<P, false, false>(g, ph, mode, src, dst, tt, Rows{1, g.ny - 2, 1}, s);
+            return step_mode<P, false, false, TRT>(g, ph, mode, src, dst, tt, Rows{1, g.ny - 2, 1}, s);
         }
-        if (g.has_mask) return step_mode<P, false, true>(g, ph, mode, src, dst, tt, all, s);
-        return step_mode<P, false, false>(g, ph, mode, src, dst, tt, all, s);
+        if (g.has_mask) return step_mode<P, false, true, TRT>(g, ph, mode, src, dst, tt, all, s);
+        return step_mode<P, false, false, TRT>(g, ph, mode, src, dst, tt, all, s);
     }
-    if (g.has_mask) return step_mode<P, true, true>(g, ph, mode, src, dst, tt, all, s);
-    return step_mode<P, true, false>(g, ph, mode, src, dst, tt, all, s);
+    if (g.has_mask) return step_mode<P, true, true, TRT>(g, ph, mode, src, dst, tt, all, s);
+    return step_mode<P, true, false, TRT>(g, ph, mode, src, dst, tt, all, s);
 }
 
 static inline dim3 node_blocks(const Geo &g) {
@@ -1780,9 +1899,11 @@ cudaError_t launch_macros_adjoint(const Geo &g, const Phys &ph, const void *stat
     return cudaGetLastError();
 }
 
+#define LBM_INSTANTIATE_STEP(P, TRT)                                                                        \
+    template cudaError_t launch_step_op<P, TRT>(const Geo &, const Phys &, int, const void *, void *,          \
+                                                unsigned long long, cudaStream_t);
 #define LBM_INSTANTIATE(P)                                                                                  \
-    template cudaError_t launch_step<P>(const Geo &, const Phys &, int, const void *, void *, unsigned long long, \
-                                        cudaStream_t);                                                      \
+    LBM_INSTANTIATE_STEP(P, false)                                                                          \
     template cudaError_t launch_init<P>(const Geo &, int, const void *, const void *, void *, cudaStream_t); \
     template cudaError_t launch_set_f<P>(const Geo &, int, const void *, void *, cudaStream_t);             \
     template cudaError_t launch_get_f<P>(const Geo &, int, const void *, void *, cudaStream_t);             \

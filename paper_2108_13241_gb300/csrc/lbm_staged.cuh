@@ -251,7 +251,7 @@ __device__ __forceinline__ void stage_tile(const Geo &g, const R *src, unsigned 
 
 // Node K (0 or 1) of the thread's 2-node vector at (lx0 + K, ly): gather from
 // the stage, bounce-back, open sides, collision, encode into out[i].v[K].
-template <class S, int FORCE, bool OPEN, int K>
+template <class S, int FORCE, bool OPEN, int K, bool TRT>
 __device__ __forceinline__ void staged_node(const Geo &g, const Phys &ph, const typename S::R *sd, int lx0, int ly,
                                             int gx0, int gy, unsigned m, const Coef<typename S::C> &co, SrState &sr,
                                             V16<typename S::R, 2> out[9]) {
@@ -286,7 +286,7 @@ __device__ __forceinline__ void staged_node(const Geo &g, const Phys &ph, const 
     }
     if constexpr (OPEN) apply_open<C, S::SCALE>(g, ph, gx0 + K, gy, m, f);
     const C Fx = PC<C>::fx(ph), Fy = PC<C>::fy(ph);
-    collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE>(f, Fx, Fy, co);
+    collide<C, FORCE != FORCE_NONE, (sizeof(C) == 4 && !S::STOCHASTIC), S::SCALE, TRT>(f, Fx, Fy, co);
     if constexpr (S::STOCHASTIC) {
         put_sr<S, K>(f, sr, (long long)gy * g.nx + gx0, out);
     } else {
@@ -319,7 +319,7 @@ template <int P> constexpr int staged_smem_bytes() {
     return StagedDepth<P>::value * StageLayout<typename St<P>::R>::BYTES;
 }
 
-template <int P, int FORCE, bool OPEN>
+template <int P, int FORCE, bool OPEN, bool TRT>
 __global__ void __launch_bounds__(STG_THREADS, StagedBlocks<P>::value)
     k_step_staged(const Geo g, const Phys ph, const void *src_v, void *dst_v, unsigned step) {
     typedef StV<P, 2> S;
@@ -404,8 +404,8 @@ __global__ void __launch_bounds__(STG_THREADS, StagedBlocks<P>::value)
             const int gx0 = (xy & 0xFFFF) * TILE + lx0, gy = (xy >> 16) * TILE + ly;
             const unsigned mv = *reinterpret_cast<const unsigned short *>(st + L::MASK_OFF + ly * TILE + lx0);
             V16<R, 2> out[9];
-            staged_node<S, FORCE, OPEN, 0>(g, ph, sd, lx0, ly, gx0, gy, mv & 0xFFu, co, sr, out);
-            staged_node<S, FORCE, OPEN, 1>(g, ph, sd, lx0, ly, gx0, gy, mv >> 8, co, sr, out);
+            staged_node<S, FORCE, OPEN, 0, TRT>(g, ph, sd, lx0, ly, gx0, gy, mv & 0xFFu, co, sr, out);
+            staged_node<S, FORCE, OPEN, 1, TRT>(g, ph, sd, lx0, ly, gx0, gy, mv >> 8, co, sr, out);
             R *o = dst + (size_t)t * (9 * TILE_N) + ly * TILE + lx0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) st16<R, 2>(o + i * TILE_N, out[i]);

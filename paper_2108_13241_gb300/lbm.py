@@ -32,6 +32,8 @@ LBM_TWO_LATTICE, LBM_AA = 0, 1
 PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S}
 LAYOUTS = {"dense": LBM_DENSE, "sparse": LBM_SPARSE_TILE16}
 PATTERNS = {"two_lattice": LBM_TWO_LATTICE, "aa": LBM_AA}
+LBM_BGK, LBM_TRT = 0, 1
+COLLISIONS = {"bgk": LBM_BGK, "trt": LBM_TRT}
 STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16S: 2}
 
 
@@ -59,6 +61,7 @@ class lbm_params(ctypes.Structure):
         ("west", lbm_side), ("east", lbm_side), ("south", lbm_side), ("north", lbm_side),
         ("precision", ctypes.c_int), ("layout", ctypes.c_int), ("pattern", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("collision", ctypes.c_int), ("magic", ctypes.c_double),
     ]
 
 
@@ -353,10 +356,11 @@ def lbm_last_error(ctx) -> str:
 def make_params(nx: int, ny: int, tau: float, solid: Optional[np.ndarray] = None,
                 force=(0.0, 0.0), periodic_x: bool = True, periodic_y: bool = True,
                 walls=None, precision="f32", layout="dense", pattern="two_lattice",
-                stream=None, open=None):
+                stream=None, open=None, collision="bgk", magic=0.0):
     """lbm_params from Python values.  walls: {"west"|"east"|"south"|"north":
     (ux, uy)} velocities of wall sides (axes not periodic).  open: {side name:
-    ("velocity", (ux, uy)) | ("pressure", rho)} open sides.  Returns
+    ("velocity", (ux, uy)) | ("pressure", rho)} open sides.  collision: "bgk"
+    or "trt" (magic: the TRT magic parameter, 0 = 3/16).  Returns
     (params, keepalive) -- keepalive holds the solid array while params is used."""
     p = lbm_params()
     p.nx, p.ny = int(nx), int(ny)
@@ -385,6 +389,8 @@ def make_params(nx: int, ny: int, tau: float, solid: Optional[np.ndarray] = None
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
     p.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
+    p.collision = COLLISIONS[collision] if isinstance(collision, str) else int(collision)
+    p.magic = float(magic)
     if stream is None and torch.cuda.is_available():
         stream = torch.cuda.current_stream().cuda_stream
     p.stream = stream or None
@@ -396,10 +402,12 @@ class LBM:
 
     def __init__(self, nx: int, ny: int, tau: float, solid=None, force=(0.0, 0.0),
                  periodic_x: bool = True, periodic_y: bool = True, walls=None,
-                 precision="f32", layout="dense", pattern="two_lattice", device="cuda", open=None):
+                 precision="f32", layout="dense", pattern="two_lattice", device="cuda", open=None,
+                 collision="bgk", magic=0.0):
         self.nx, self.ny = int(nx), int(ny)
         self.params, keep = make_params(nx, ny, tau, solid, force, periodic_x, periodic_y, walls,
-                                        precision, layout, pattern, open=open)
+                                        precision, layout, pattern, open=open, collision=collision,
+                                        magic=magic)
         self.precision = self.params.precision
         self.dtype = torch.float64 if self.precision == LBM_F64 else torch.float32
         self.device = torch.device(device)
