@@ -561,6 +561,10 @@ def extra_measurements(args):
     t = run(dict(nx=n, ny=n, tau=0.8, force=(fx, 0.0), periodic_y=False), rho_p, u_p, "f32", "dense",
             "two_lattice", 500)
     record("poiseuille_%d/f32/dense/two_lattice" % n, n * n, 500, t, "f32")
+    # the same channel with the two-relaxation-time collision (Lambda = 3/16)
+    t = run(dict(nx=n, ny=n, tau=0.8, force=(fx, 0.0), periodic_y=False, collision="trt", magic=3.0 / 16.0),
+            rho_p, u_p, "f32", "dense", "two_lattice", 500)
+    record("poiseuille_%d/f32/dense/two_lattice/trt" % n, n * n, 500, t, "f32")
     for phi in (0.2, 0.5, 0.8):
         solid, achieved, _ = inputs.porous_discs(n, n, phi, rmin=8, rmax=32)
         nf = int((solid == 0).sum())
