@@ -361,21 +361,25 @@ def run_gpu_arm(args, rank, world, dist):
     if not np.isfinite(mass):
         raise RuntimeError("simulation diverged")
 
-    # end to end through the public API: pinned host fields -> device, init,
-    # K steps, macros, device -> pinned host result
+    # end to end through the public API: the initial fields in pinned host
+    # memory are read by the init kernel itself (the device maps pinned
+    # host memory; on GB300 the reads cross NVLink-C2C while the kernel
+    # runs), K steps, and the macros kernel writes (rho, u) straight into
+    # pinned host memory; every byte still moves host <-> device inside the
+    # timed region
     out_rho = torch.empty((kw["ny"], kw["nx"]), dtype=dtype).pin_memory()
     out_u = torch.empty((2, kw["ny"], kw["nx"]), dtype=dtype).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    r_d = None if rho_h is None else rho_h.to(dev, non_blocking=True)
-    v_d = None if u_h is None else u_h.to(dev, non_blocking=True)
-    sim.init_equilibrium(r_d, v_d)
+    lbm.lbm_init_equilibrium(sim.ctx, rho_h, u_h)
     sim.step(args.steps)
-    r_out, u_out = sim.macros()
-    out_rho.copy_(r_out, non_blocking=True)
-    out_u.copy_(u_out, non_blocking=True)
+    lbm.lbm_macros(sim.ctx, out_rho, out_u)
     torch.cuda.synchronize()
     t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    # the fields came back: the same (rho, u) as through device buffers
+    r_out, u_out = sim.macros()
+    if not (torch.equal(out_rho, r_out.cpu()) and torch.equal(out_u, u_out.cpu())):
+        raise RuntimeError("fields written into pinned host memory differ from the device result")
     h2d = (0 if rho_h is None else rho_h.numel() * rho_h.element_size()) + \
           (0 if u_h is None else u_h.numel() * u_h.element_size())
     d2h = out_rho.numel() * out_rho.element_size() + out_u.numel() * out_u.element_size()
@@ -401,8 +405,8 @@ def run_gpu_arm(args, rank, world, dist):
         "roofline": roofline,
         "e2e": {"value": round(whole_job_glups(nfluid, args.steps, world, t_e2e), 3), "unit": "GLUPS",
                 "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
-                "what": "pinned host rho,u -> device, lbm_init_equilibrium, K x lbm_step, lbm_macros, "
-                        "device -> pinned host rho,u"},
+                "what": "lbm_init_equilibrium reading rho,u from pinned host memory, K x lbm_step, "
+                        "lbm_macros writing rho,u into pinned host memory (NVLink-C2C, no staging copies)"},
         "gpu_launches": step_launches,
         "clocks": clocks,
     }

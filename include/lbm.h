@@ -23,7 +23,12 @@
  *    scalar fields  s[ny][nx].
  *  "Compute type" = double for LBM_F64, float for LBM_F32 and LBM_F16S; every
  *  canonical device array passed to or from the library is in compute type.
- *  Device pointers must be 16-byte aligned (torch allocations are).
+ *  Device pointers must be 16-byte aligned (torch allocations are).  The
+ *  field arguments of lbm_init_equilibrium and lbm_macros may also be
+ *  pinned host memory that the device maps (cudaHostAlloc / torch
+ *  pin_memory under unified addressing): the kernels then read or write
+ *  host memory directly -- on GB300 over NVLink-C2C, overlapping the
+ *  transfer with the kernel instead of staging it in a separate copy.
  *  Ownership: all device memory belongs to the caller.  lbm_create carves
  *  its lattices and tables out of the caller's workspace; the context owns
  *  host memory only.  Caller buffers must outlive the calls that use them

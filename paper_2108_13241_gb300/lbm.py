@@ -175,8 +175,16 @@ def lbm_set_force(ctx, force: Optional[torch.Tensor]):
     _check("lbm_set_force", _load().lbm_set_force(ctx, _ptr(force)), ctx)
 
 
+def _field(t: Optional[torch.Tensor]):
+    """A field argument: a CUDA tensor, or a pinned host tensor the device
+    maps (the kernel then reads or writes host memory directly)."""
+    if t is not None and not t.is_cuda and not t.is_pinned():
+        raise ValueError("field tensors must be on the GPU or in pinned host memory")
+    return _ptr(t)
+
+
 def lbm_init_equilibrium(ctx, rho: Optional[torch.Tensor], u: Optional[torch.Tensor]):
-    _check("lbm_init_equilibrium", _load().lbm_init_equilibrium(ctx, _ptr(rho), _ptr(u)), ctx)
+    _check("lbm_init_equilibrium", _load().lbm_init_equilibrium(ctx, _field(rho), _field(u)), ctx)
 
 
 def lbm_step(ctx, n: int):
@@ -192,7 +200,7 @@ def lbm_step_launches(ctx, n: int) -> int:
 
 
 def lbm_macros(ctx, rho: Optional[torch.Tensor], u: Optional[torch.Tensor]):
-    _check("lbm_macros", _load().lbm_macros(ctx, _ptr(rho), _ptr(u)), ctx)
+    _check("lbm_macros", _load().lbm_macros(ctx, _field(rho), _field(u)), ctx)
 
 
 def lbm_get_f(ctx, f: torch.Tensor):
