@@ -395,6 +395,12 @@ def run_gpu_arm(args, rank, world, dist):
                 "frac_of_nominal_8000_gbs": round(achieved / 8000.0, 4),
                 "traffic": profiled_traffic(prof_name),
                 "algorithmic_bytes_per_launch": algo, "kernel": "k_step (%s)" % prof_name}
+    if kw.get("solid") is not None and args.pattern == "two_lattice":
+        # porous workloads: the geometry's fluid DRAM sectors copied without
+        # arithmetic (lbm_sector_copy), what HBM delivers for its pattern
+        nbytes, tc = sector_copy_time(sim, args.steps, stream)
+        roofline["sector_copy"] = {"bytes_per_copy": nbytes, "GBps": round(nbytes / tc / 1e9, 1),
+                                   "frac_of_sector_copy": round(tc / step_s, 4)}
     res = {
         "metric": METRIC, "value": round(glups, 3), "unit": "GLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 5),
@@ -514,6 +520,23 @@ def _timed(sim, k, stream):
     return time_steps(sim, k, 10, stream)
 
 
+def sector_copy_time(sim, k: int, stream):
+    """(bytes, seconds) of one lbm_sector_copy: the geometry's fluid DRAM
+    sectors, all nine slots, read and written once, no arithmetic; the mean
+    of k back-to-back copies after 5 warm-up ones, CUDA events on the
+    library's stream."""
+    import torch
+    nbytes = sim.sector_copy(5)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    sim.sector_copy(k)
+    end.record(stream)
+    end.synchronize()
+    return nbytes, start.elapsed_time(end) / 1e3 / k
+
+
 def extra_measurements(args):
     """Other rows of the metric, each with fewer steps: every precision and
     pattern on the dense Taylor-Green box, the Poiseuille channel, the porous
@@ -545,6 +568,15 @@ def extra_measurements(args):
         torch.cuda.empty_cache()
         return t
 
+    def geometry_copy(kw, prec, layout):
+        sim = lbm.LBM(precision=prec, layout=layout, pattern="two_lattice", **kw)
+        sim.init_equilibrium(None, None)
+        cp = sector_copy_time(sim, 100, stream)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        return cp
+
     n = 4096
     rho, u = inputs.taylor_green(n, n, 0.05)
     kw = dict(nx=n, ny=n, tau=0.8)
@@ -570,6 +602,7 @@ def extra_measurements(args):
             rho_p, u_p, "f32", "dense", "two_lattice", 500)
     record("poiseuille_%d/f32/dense/two_lattice/trt" % n, n * n, 500, t, "f32")
     for phi in (0.2, 0.5, 0.8):
+        copies = {}
         solid, achieved, _ = inputs.porous_discs(n, n, phi, rmin=8, rmax=32)
         nf = int((solid == 0).sum())
         kwp = dict(nx=n, ny=n, tau=0.8, solid=solid, force=(1e-6, 0.0), periodic_y=False)
@@ -587,6 +620,13 @@ def extra_measurements(args):
             sec = sector_nodes(solid, prec)
             out[key]["sector_nodes"] = sec
             out[key]["frac_of_sector_roofline"] = round(g * sec / nf * node_bytes(prec) / peak, 4)
+            # against what HBM measurably delivers for this geometry's sector
+            # pattern in this layout: the copy of its fluid sectors
+            if (prec, layout) not in copies:
+                copies[(prec, layout)] = geometry_copy(kwp, prec, layout)
+            nbytes, tc = copies[(prec, layout)]
+            out[key]["sector_copy"] = {"GBps": round(nbytes / tc / 1e9, 1),
+                                       "frac_of_sector_copy": round(tc / (t / k), 4)}
             if layout == "sparse" and (prec, layout, pattern) in dense_geom:
                 out["porous_phi%.2f_%d/%s/%s/%s" % (achieved, n, prec, layout, pattern)]["eta_P"] = round(
                     g / dense_geom[(prec, layout, pattern)], 3)
@@ -626,10 +666,12 @@ def porosity_sweep(n: int = 4096, steps: int = 300, names=None, phis=None):
         sim.init_equilibrium(None, None)
         t = time_steps(sim, steps, 10, stream)
         tiles = sim.tile_map()[1].shape[0] if layout == "sparse" else None
+        copy = sector_copy_time(sim, steps, stream) if solid is not None else None
         sim.close()
         del sim
         torch.cuda.empty_cache()
-        return nf * steps / t / 1e9, nf, tiles
+        return nf * steps / t / 1e9, nf, tiles, (None if copy is None else (copy[0] / copy[1] / 1e9,
+                                                                            copy[1] / (t / steps)))
 
     ref = {lay: glups(None, lay)[0] for lay in ("sparse", "dense")}
     res = {"all_fluid": {lay: round(g, 3) for lay, g in ref.items()}}
@@ -647,9 +689,12 @@ def porosity_sweep(n: int = 4096, steps: int = 300, names=None, phis=None):
             solid, achieved = gen(phi)
             row = {"phi": round(achieved, 4)}
             for lay in ("sparse", "dense"):
-                g, nf, tiles = glups(solid, lay)
+                g, nf, tiles, cp = glups(solid, lay)
                 row[lay] = {"GLUPS": round(g, 3), "eta_P": round(g / ref[lay], 3),
                             "frac_of_measured_hbm": round(g * node_bytes("f32") / peak, 4)}
+                if cp is not None:
+                    row[lay]["sector_copy_GBps"] = round(cp[0], 1)
+                    row[lay]["frac_of_sector_copy"] = round(cp[1], 4)
                 if tiles is not None:
                     row["kept_tiles"] = int(tiles)
                 row[lay]["frac_of_sector_roofline"] = round(

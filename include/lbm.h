@@ -306,6 +306,21 @@ lbm_status lbm_geometry(const lbm_params *p, uint8_t *h_mask, int32_t *h_tile_id
 lbm_status lbm_reduce_f_noalloc(lbm_precision precision, const void *d_f, const uint8_t *d_mask, int nx, int ny,
                                 double *d_out, void *stream);
 
+/* Measurement aid, with no counterpart in the paper: the data movement of
+ * one time step at DRAM-sector granularity without its arithmetic.  Copies,
+ * n times, every 32-byte sector (8 FP32, 16 FP16s or 4 FP64 consecutive
+ * nodes of one distribution slot) of the current lattice that holds a fluid
+ * node, in all nine slots, into the other lattice of a two-lattice context,
+ * asynchronously on the context's stream.  Any step must move at least
+ * these bytes on the geometry; timing this call measures what HBM delivers
+ * for the geometry's access pattern (scattered sectors on porous media), the
+ * ceiling the step kernels are compared with.  The state A_t (the current
+ * lattice) is not changed; the other lattice is the next step's output.
+ * h_bytes (host, may be NULL) receives the bytes one copy reads and writes,
+ * 2 * 9 * 32 * (sectors holding fluid).  LBM_ERR_UNSUPPORTED for the AA
+ * pattern (one lattice); LBM_ERR_INVALID for n < 0. */
+lbm_status lbm_sector_copy(lbm_ctx *ctx, int n, long long *h_bytes);
+
 long long lbm_fluid_nodes(const lbm_ctx *ctx);
 long long lbm_step_count(const lbm_ctx *ctx);
 

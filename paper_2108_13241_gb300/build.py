@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["lbm_api.cu", "kern_f64.cu", "kern_f32.cu", "kern_f16s.cu", "kern_f64_trt.cu", "kern_f32_trt.cu",
                 "kern_f16s_trt.cu", "lbm_noalloc.cu"]
 CXX_SOURCES = ["lbm_geometry.cpp"]
-HEADERS = ["lbm_internal.h", "lbm_kernels.cuh"]
+HEADERS = ["lbm_internal.h", "lbm_kernels.cuh", "lbm_staged.cuh"]
 
 
 def _nvcc() -> str:

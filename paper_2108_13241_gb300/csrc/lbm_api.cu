@@ -56,6 +56,8 @@ struct lbm_ctx {
     int graphs = 1;                   // replay graphs (lbm_set_graphs)
     unsigned long long *tb = nullptr; // device time-step counter of replayed steps
     unsigned long long version = 0;   // bumped when the physics' pointers change
+    long long fluid_sectors = 0;      // 32-byte sectors of one slot that hold a fluid node
+    const uint32_t *secs = nullptr;   // their list (NULL: every sector holds fluid)
 };
 
 namespace {
@@ -109,7 +111,7 @@ struct Plan {
     bool has_mask;
     long long nslot;
     size_t off_lat1, off_mask, off_nbr, off_txy, off_tid, off_part, off_out, off_tb, off_list2, off_list4, off_vmask,
-        off_order, total;
+        off_order, off_hmask, off_sec, total;
     size_t lat_bytes, mask_bytes;
     bool use_list;
 };
@@ -127,6 +129,9 @@ struct SparseTables {
     // per tile 128 bytes: the 2-node vectors (8 * row + v) of the DRAM
     // sectors (32 bytes of one slot) that hold a fluid node, then 0xFF
     std::vector<uint8_t> order;
+    // two-lattice contexts with a mask: the 32-byte sectors of a slot that
+    // hold a fluid node, ascending (lbm_sector_copy)
+    std::vector<uint32_t> secs;
 };
 
 // The staged step's tables: per tile, which 2-node vectors hold fluid (it
@@ -181,6 +186,39 @@ void build_vector_lists(int ntiles, const std::vector<uint8_t> &tmask, int sec, 
                 if (sector) out.push_back((uint32_t)t * (uint32_t)tpt + (uint32_t)k);
             }
     }
+}
+
+// The 32-byte sectors (e consecutive nodes of a slot: 8 FP32, 16 FP16s, 4
+// FP64; never across a row or tile row, nx being a multiple of 16) that hold
+// a fluid node, ascending.
+void fluid_sectors(const std::vector<uint8_t> &mask, long long nslot, int e, std::vector<uint32_t> &out) {
+    out.clear();
+    for (long long k = 0; k + e <= nslot; k += e) {
+        bool f = false;
+        for (int j = 0; j < e; ++j) f = f || mask[(size_t)(k + j)] != 0xFF;
+        if (f) out.push_back((uint32_t)(k / e));
+    }
+}
+
+// The staged step's halo masks: per tile 4 words, bit h of word h / 32 set
+// iff halo chunk h (halo_source, E values of esize bytes) comes from an
+// existing neighbour (nbr3: [tile][3 x 3]) and its E source nodes include a
+// fluid node.  Only unbounced pulls read a halo value, and they pull from
+// fluid nodes, so the other chunks need not be read.
+void build_halo_masks(int ntiles, const std::vector<uint8_t> &tmask, const std::vector<int32_t> &nbr3, size_t esize,
+                      std::vector<uint32_t> &out) {
+    const int E = (int)(16 / esize);
+    const int nh = halo_chunks(E) < 128 ? halo_chunks(E) : 128;
+    out.assign((size_t)ntiles * 4, 0u);
+    for (int t = 0; t < ntiles; ++t)
+        for (int h = 0; h < nh; ++h) {
+            const HaloSrc hs = halo_source(h, E);
+            const int n = nbr3[(size_t)t * 9 + hs.dir];
+            if (n < 0) continue;
+            bool f = false;
+            for (int j = 0; j < E; ++j) f = f || tmask[(size_t)n * TILE_N + hs.srow * TILE + hs.scol + j] != 0xFF;
+            if (f) out[(size_t)t * 4 + h / 32] |= 1u << (h % 32);
+        }
 }
 
 // Geometry tables and the workspace layout for p.
@@ -248,7 +286,56 @@ void make_plan(const lbm_params &p, std::vector<uint8_t> &mask, std::vector<int3
     if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntiles * 16);
     pl.off_order = off;
     if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntiles * (TILE_N / 2));
+    pl.off_hmask = off;
+    if (p.layout == LBM_SPARSE_TILE16) off += align256((size_t)pl.ntiles * 16);
+    // the sector copy's list (two-lattice with a mask; without one every
+    // sector holds fluid)
+    sp.secs.clear();
+    if (p.pattern == LBM_TWO_LATTICE && (p.layout == LBM_SPARSE_TILE16 || pl.has_mask))
+        fluid_sectors(p.layout == LBM_SPARSE_TILE16 ? sp.tmask : mask, pl.nslot, 32 / (int)es, sp.secs);
+    pl.off_sec = off;
+    off += align256(sp.secs.size() * 4);
     pl.total = off;
+}
+
+// Measurement aid: the listed 32-byte sectors (list NULL: every sector) of
+// all nine slots, copied src -> dst in uint4 units.  Sector k of a slot is
+// sector k % sb of block k / sb, a block being the whole slot in the dense
+// layout (f[i][y][x], sb = the slot's sectors) and one tile in the tiled
+// layout (f[tile][i][256], sb = a tile slot's sectors).  SLOT_MAJOR false:
+// consecutive threads take the 18 halves (9 slots x 2) of one sector, so a
+// warp's accesses stay within about two tiles' 9 KB (tiled layout);
+// true: consecutive threads take 16 consecutive listed sectors of one slot
+// (dense layout, whose slots lie nslot elements apart).
+constexpr int SC_BLOCK = 256;
+template <bool SLOT_MAJOR>
+__global__ void __launch_bounds__(SC_BLOCK) k_sector_copy(const uint4 *src, uint4 *dst, const uint32_t *list,
+                                                          long long nsec, long long sb) {
+    // threads: 18 per sector (SLOT_MAJOR: 288 per group of 16 sectors, the
+    // last group possibly partial)
+    const long long tot = SLOT_MAJOR ? (nsec + 15) / 16 * 288 : nsec * 18;
+    for (long long q = (long long)blockIdx.x * SC_BLOCK + threadIdx.x; q < tot; q += (long long)gridDim.x * SC_BLOCK) {
+        long long e;
+        int i, h;
+        if constexpr (SLOT_MAJOR) {
+            // groups of 16 sectors: 9 slots x 32 threads (16 sectors x 2 halves)
+            const long long grp = q / 288;
+            const int w = (int)(q - 288 * grp);
+            i = w >> 5;
+            e = grp * 16 + ((w & 31) >> 1);
+            h = w & 1;
+            if (e >= nsec) continue;
+        } else {
+            e = q / 18;
+            const int r = (int)(q - 18 * e);
+            i = r >> 1;
+            h = r & 1;
+        }
+        const long long k = list ? (long long)__ldg(list + e) : e;
+        const long long blk = k / sb;
+        const long long off = (blk * 9 + i) * (2 * sb) + 2 * (k - blk * sb) + h;
+        dst[off] = src[off];
+    }
 }
 
 lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg) {
@@ -441,6 +528,10 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     c->esize = elem_size(p->precision);
     c->csize = comp_size(p->precision);
     c->nfluid = pl.nfluid;
+    const bool listed = p->pattern == LBM_TWO_LATTICE && (p->layout == LBM_SPARSE_TILE16 || pl.has_mask);
+    c->fluid_sectors = listed ? (long long)sp.secs.size() : pl.nslot * (long long)elem_size(p->precision) / 32;
+    c->secs = listed ? reinterpret_cast<const uint32_t *>(reinterpret_cast<char *>(d_workspace) + pl.off_sec)
+                     : nullptr;
     c->lat_bytes = pl.lat_bytes;
     char *ws = reinterpret_cast<char *>(d_workspace);
     c->lat[0] = ws;
@@ -550,6 +641,9 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
     if (!st) st = cuda_check(c, cudaMemsetAsync(ws + pl.off_tb, 0, 256, s), "memset counter");
     if (!st && p->pattern == LBM_TWO_LATTICE)
         st = cuda_check(c, cudaMemsetAsync(c->lat[1], 0, pl.lat_bytes, s), "memset lattice");
+    if (!st && !sp.secs.empty())
+        st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_sec, sp.secs.data(), sp.secs.size() * 4,
+                                           cudaMemcpyHostToDevice, s), "copy sector list");
     if (!st && p->layout == LBM_DENSE && pl.mask_bytes)
         st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_mask, c->mask.data(), pl.mask_bytes,
                                            cudaMemcpyHostToDevice, s), "copy mask");
@@ -584,6 +678,13 @@ lbm_status lbm_create(const lbm_params *p, void *d_workspace, size_t bytes, lbm_
         if (!st)
             st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_order, sp.order.data(), sp.order.size(),
                                                cudaMemcpyHostToDevice, s), "copy vector order");
+        std::vector<uint32_t> hmask;
+        build_halo_masks(pl.ntiles, tmask, nbr3, elem_size(p->precision), hmask);
+        if (!st)
+            st = cuda_check(c, cudaMemcpyAsync(ws + pl.off_hmask, hmask.data(), hmask.size() * 4,
+                                               cudaMemcpyHostToDevice, s), "copy halo masks");
+        if (!st) st = cuda_check(c, cudaStreamSynchronize(s), "upload tables");
+        g.tile_hmask = reinterpret_cast<const uint4 *>(ws + pl.off_hmask);
         g.tile_vmask = reinterpret_cast<const uint4 *>(ws + pl.off_vmask);
         g.tile_order = reinterpret_cast<const uint8_t *>(ws + pl.off_order);
         g.nbr = reinterpret_cast<const int32_t *>(ws + pl.off_nbr);
@@ -620,6 +721,36 @@ lbm_status lbm_destroy(lbm_ctx *ctx) {
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     delete ctx;
     return LBM_OK;
+}
+
+lbm_status lbm_sector_copy(lbm_ctx *ctx, int n, long long *h_bytes) {
+    LBM_CTX_CHECK(ctx);
+    if (n < 0) return fail(ctx, LBM_ERR_INVALID, "n < 0");
+    if (ctx->p.pattern != LBM_TWO_LATTICE)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "the sector copy writes the other lattice of a two-lattice context");
+    const bool tiled = ctx->geo.layout == LBM_SPARSE_TILE16;
+    const long long sb = (tiled ? (long long)TILE_N : ctx->geo.nslot) * (long long)ctx->esize / 32;
+    if (h_bytes) *h_bytes = 2ll * 9 * 32 * ctx->fluid_sectors;
+    if (n == 0 || ctx->fluid_sectors == 0) return LBM_OK;
+    // eight blocks per SM, grid-stride (measured best for this copy)
+    static const int grid = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return (sms > 0 ? sms : 1) * 8;
+    }();
+    const uint4 *src = reinterpret_cast<const uint4 *>(ctx->lat[ctx->cur]);
+    uint4 *dst = reinterpret_cast<uint4 *>(ctx->lat[1 - ctx->cur]);
+#ifndef LBM_SC_DENSE_SLOT_MAJOR
+#define LBM_SC_DENSE_SLOT_MAJOR 1
+#endif
+    for (int j = 0; j < n; ++j) {
+        if (tiled || !LBM_SC_DENSE_SLOT_MAJOR)
+            k_sector_copy<false><<<grid, SC_BLOCK, 0, ctx->stream>>>(src, dst, ctx->secs, ctx->fluid_sectors, sb);
+        else
+            k_sector_copy<true><<<grid, SC_BLOCK, 0, ctx->stream>>>(src, dst, ctx->secs, ctx->fluid_sectors, sb);
+    }
+    return cuda_check(ctx, cudaGetLastError(), "sector copy launch");
 }
 
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable) {

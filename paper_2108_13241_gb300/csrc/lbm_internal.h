@@ -17,6 +17,54 @@ constexpr int AUX_BLOCK = 256;  // threads per block of the per-node kernels
 constexpr int RED_BLOCKS = 608; // blocks of the reduction pass (4 x 152 SMs)
 constexpr int WALL_SIDES = 5;   // W, E, S, N, and "solid obstacle" (term 0)
 
+// Halo chunk h of the staged tiled step's stage (E stored values = 16 bytes
+// of one tile row): which slot it serves, the neighbour it comes from
+// (3 x 3 index dir = 3 (oy + 1) + (ox + 1)), its source row and first
+// column in that tile, and where it lands around the tile core (dlx: -E or
+// 16 for a column chunk, else its first column; dly: -1 or 16 for a row
+// chunk, else its row).  Chunks 0 .. 3 CPR - 1: the row below (slots 2, 5,
+// 6 pulling from y - 1), then the row above (4, 7, 8), the left column (1,
+// 5, 8; one chunk per row), the right column (3, 6, 7), and the four
+// corners (5 SW, 6 SE, 7 NE, 8 NW).  Shared by the kernel, which copies the
+// chunks, and the host, which marks the ones whose source holds fluid.
+struct HaloSrc {
+    int dir, slot, srow, scol, dlx, dly;
+};
+__host__ __device__ constexpr int halo_chunks(int E) { return 6 * (TILE / E) + 6 * TILE + 4; }
+__host__ __device__ inline HaloSrc halo_source(int h, int E) {
+    const int CPR = TILE / E;
+    HaloSrc c;
+    int ox, oy;
+    if (h < 3 * CPR) { // row below the tile (ly = -1)
+        const int s3 = h / CPR, k = h - s3 * CPR;
+        c.slot = s3 == 0 ? 2 : (s3 == 1 ? 5 : 6);
+        ox = 0; oy = -1; c.srow = TILE - 1; c.scol = k * E; c.dly = -1; c.dlx = k * E;
+    } else if (h < 6 * CPR) { // row above (ly = 16)
+        const int hh = h - 3 * CPR, s3 = hh / CPR, k = hh - s3 * CPR;
+        c.slot = s3 == 0 ? 4 : (s3 == 1 ? 7 : 8);
+        ox = 0; oy = 1; c.srow = 0; c.scol = k * E; c.dly = TILE; c.dlx = k * E;
+    } else if (h < 6 * CPR + 3 * TILE) { // left column chunk
+        const int hh = h - 6 * CPR, s3 = hh / TILE, r = hh - s3 * TILE;
+        c.slot = s3 == 0 ? 1 : (s3 == 1 ? 5 : 8);
+        ox = -1; oy = 0; c.srow = r; c.scol = TILE - E; c.dly = r; c.dlx = -E;
+    } else if (h < 6 * CPR + 6 * TILE) { // right column chunk
+        const int hh = h - 6 * CPR - 3 * TILE, s3 = hh / TILE, r = hh - s3 * TILE;
+        c.slot = s3 == 0 ? 3 : (s3 == 1 ? 6 : 7);
+        ox = 1; oy = 0; c.srow = r; c.scol = 0; c.dly = r; c.dlx = TILE;
+    } else { // corners, one diagonal slot each
+        const int k = h - 6 * CPR - 6 * TILE;
+        c.slot = 5 + k;
+        ox = (k == 0 || k == 3) ? -1 : 1;
+        oy = (k <= 1) ? -1 : 1;
+        c.srow = oy < 0 ? TILE - 1 : 0;
+        c.scol = ox < 0 ? TILE - E : 0;
+        c.dly = oy < 0 ? -1 : TILE;
+        c.dlx = ox < 0 ? -E : TILE;
+    }
+    c.dir = 3 * (oy + 1) + (ox + 1);
+    return c;
+}
+
 // Kernel kinds of one time step.
 enum StepMode {
     MODE_TWO_LATTICE = 0, // gather from src, store aligned into dst
@@ -59,6 +107,10 @@ struct Geo {
     // sparse: per tile 128 bytes, the 2-node vectors (8 * row + v) whose
     // 32-byte DRAM sector holds a fluid node, ascending, then 0xFF
     const uint8_t *tile_order;
+    // sparse: per tile 128 bits, bit h (word h / 32) set iff halo chunk h of
+    // the staged step (halo_source) exists and its source holds a fluid
+    // node; the other chunks are never pulled unbounced, and are not read
+    const uint4 *tile_hmask;
     // device error word: set when a kernel's bounded wait gave up
     unsigned *err;
 };

@@ -21,7 +21,9 @@
 //    and one 16-byte halo chunk of columns on exactly the edges that slot
 //    pulls across, filled from the 3 x 3 neighbour tiles -- so the pull
 //    f'_i(x) = A_i(x - c_i) is one shared-memory load at a fixed offset, with
-//    no per-node test of tile edges;
+//    no per-node test of tile edges; a halo chunk whose source nodes are all
+//    solid (the tile's host-built halo mask) is zero-filled, not read, since
+//    only unbounced pulls, from fluid nodes, use halo values;
 //  * four consumer warps take the tile's 2-node vectors from a per-tile list
 //    of the vectors whose DRAM sector holds fluid (host-built), so a consumer
 //    warp whose share of a porous tile is solid skips the collision;
@@ -123,7 +125,8 @@ template <class R> struct StageLayout {
         return base(i) + (ly + hs(i)) * rp(i) + lx + hw(i);
     }
     static constexpr int DATA = base(8) + size(8);         // elements of the 9 slots
-    static constexpr int HALO = 6 * CPR + 6 * TILE + 4;    // halo chunks
+    static constexpr int HALO = halo_chunks(E);            // halo chunks
+    static_assert(HALO <= 128, "one bit per halo chunk in the tile's 128-bit halo mask");
     static constexpr int HALO_ROUNDS = (HALO + 31) / 32;   // per producer lane
     static constexpr int POS_ROUNDS = TILE * CPR / 32;     // (row, chunk) positions per lane
     static constexpr int MASK_OFF = DATA * (int)sizeof(R); // 256 node mask bytes
@@ -144,42 +147,15 @@ struct HaloChunk {
 
 template <class R> __device__ __forceinline__ HaloChunk halo_chunk(int h) {
     typedef StageLayout<R> L;
-    constexpr int E = L::E, CPR = L::CPR;
+    const HaloSrc hs = halo_source(h, L::E);
     HaloChunk c;
-    int slot, ox, oy, srow, scol, dlx, dly;
-    if (h < 3 * CPR) { // row below the tile (ly = -1): slots pulling from y - 1
-        const int s3 = h / CPR, k = h - s3 * CPR;
-        slot = s3 == 0 ? 2 : (s3 == 1 ? 5 : 6);
-        ox = 0; oy = -1; srow = TILE - 1; scol = k * E; dly = -1; dlx = k * E;
-    } else if (h < 6 * CPR) { // row above (ly = 16): slots pulling from y + 1
-        const int hh = h - 3 * CPR, s3 = hh / CPR, k = hh - s3 * CPR;
-        slot = s3 == 0 ? 4 : (s3 == 1 ? 7 : 8);
-        ox = 0; oy = 1; srow = 0; scol = k * E; dly = TILE; dlx = k * E;
-    } else if (h < 6 * CPR + 3 * TILE) { // left column chunk: slots pulling from x - 1
-        const int hh = h - 6 * CPR, s3 = hh / TILE, r = hh - s3 * TILE;
-        slot = s3 == 0 ? 1 : (s3 == 1 ? 5 : 8);
-        ox = -1; oy = 0; srow = r; scol = TILE - E; dly = r; dlx = -E;
-    } else if (h < 6 * CPR + 6 * TILE) { // right column chunk: slots pulling from x + 1
-        const int hh = h - 6 * CPR - 3 * TILE, s3 = hh / TILE, r = hh - s3 * TILE;
-        slot = s3 == 0 ? 3 : (s3 == 1 ? 6 : 7);
-        ox = 1; oy = 0; srow = r; scol = 0; dly = r; dlx = TILE;
-    } else { // corners, one diagonal slot each
-        const int k = h - 6 * CPR - 6 * TILE;
-        slot = 5 + k; // 5 SW, 6 SE, 7 NE, 8 NW
-        ox = (k == 0 || k == 3) ? -1 : 1;
-        oy = (k <= 1) ? -1 : 1;
-        srow = oy < 0 ? TILE - 1 : 0;
-        scol = ox < 0 ? TILE - E : 0;
-        dly = oy < 0 ? -1 : TILE;
-        dlx = ox < 0 ? -E : TILE;
-    }
-    c.dir = 3 * (oy + 1) + (ox + 1);
-    c.src = (unsigned)(slot * TILE_N + srow * TILE + scol);
+    c.dir = hs.dir;
+    c.src = (unsigned)(hs.slot * TILE_N + hs.srow * TILE + hs.scol);
     // the slot-specific layout, evaluated per slot (slot is not a constant here)
     unsigned d = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        if (i == slot) d = (unsigned)L::at(i, dlx, dly);
+        if (i == hs.slot) d = (unsigned)L::at(i, hs.dlx, hs.dly);
     c.dst = d;
     return c;
 }
@@ -188,7 +164,7 @@ template <class R> __device__ __forceinline__ HaloChunk halo_chunk(int h) {
 template <int HR> struct TileRec {
     int t;      // tile id (< 0: nothing to stage)
     uint4 vm;   // 2-node vectors holding fluid: bit 8 * (row % 4) + v of word row / 4
-    int nb[HR]; // neighbour tile of this lane's halo chunks (-1 absent)
+    int nb[HR]; // neighbour tile of this lane's halo chunks (-1: absent, or no fluid at the source)
 };
 
 template <class R, int HR>
@@ -199,6 +175,13 @@ __device__ __forceinline__ void load_rec(const Geo &g, int t, const HaloChunk (&
     r.vm = __ldg(g.tile_vmask + t);
 #pragma unroll
     for (int k = 0; k < HR; ++k) r.nb[k] = (lane + 32 * k < L::HALO) ? __ldg(g.nbr + 9 * t + hc[k].dir) : -1;
+    // halo chunks whose source holds no fluid are zero-filled, not read
+    const uint4 hm = __ldg(g.tile_hmask + t);
+#pragma unroll
+    for (int k = 0; k < HR; ++k) {
+        const unsigned w = k == 0 ? hm.x : (k == 1 ? hm.y : (k == 2 ? hm.z : hm.w));
+        if (!((w >> lane) & 1u)) r.nb[k] = -1;
+    }
 }
 
 // Fluid bits of tile row `row` (bit v: 2-node vector v of the row holds a

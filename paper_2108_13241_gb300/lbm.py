@@ -106,6 +106,7 @@ def _load():
         "lbm_step_count": ([_vp], ctypes.c_longlong),
         "lbm_launches_per_step": ([_vp], ctypes.c_int),
         "lbm_set_graphs": ([_vp, ctypes.c_int], st),
+        "lbm_sector_copy": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)], st),
         "lbm_step_launches": ([_vp, ctypes.c_int], ctypes.c_longlong),
         "lbm_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lbm_last_error": ([_vp], ctypes.c_char_p),
@@ -193,6 +194,13 @@ def lbm_step(ctx, n: int):
 
 def lbm_set_graphs(ctx, enable: bool):
     _check("lbm_set_graphs", _load().lbm_set_graphs(ctx, int(bool(enable))), ctx)
+
+
+def lbm_sector_copy(ctx, n: int) -> int:
+    """Launches n sector copies (measurement aid); returns the bytes of one."""
+    b = ctypes.c_longlong(0)
+    _check("lbm_sector_copy", _load().lbm_sector_copy(ctx, int(n), ctypes.byref(b)), ctx)
+    return int(b.value)
 
 
 def lbm_step_launches(ctx, n: int) -> int:
@@ -455,6 +463,11 @@ class LBM:
     def step_launches(self, n: int) -> int:
         """Kernel launches that step(n) makes (graph nodes included)."""
         return lbm_step_launches(self.ctx, n)
+
+    def sector_copy(self, n: int = 1) -> int:
+        """n copies of the lattice's fluid-holding DRAM sectors into the
+        other lattice (lbm_sector_copy); returns the bytes of one copy."""
+        return lbm_sector_copy(self.ctx, n)
 
     def set_graphs(self, enable: bool):
         """Replay CUDA graphs for long step runs (default) or launch every
