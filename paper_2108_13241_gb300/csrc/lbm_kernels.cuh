@@ -206,6 +206,18 @@ __device__ __forceinline__ float shfl_down1(float v) { return __shfl_down_sync(L
 __device__ __forceinline__ unsigned short shfl_down1(unsigned short v) {
     return (unsigned short)__shfl_down_sync(LBM_FULL, (unsigned)v, 1);
 }
+// the same among the lanes of mask m (a lane outside m gives an undefined
+// value, which the caller does not use)
+__device__ __forceinline__ double shfl_up1(unsigned m, double v) { return __shfl_up_sync(m, v, 1); }
+__device__ __forceinline__ float shfl_up1(unsigned m, float v) { return __shfl_up_sync(m, v, 1); }
+__device__ __forceinline__ unsigned short shfl_up1(unsigned m, unsigned short v) {
+    return (unsigned short)__shfl_up_sync(m, (unsigned)v, 1);
+}
+__device__ __forceinline__ double shfl_down1(unsigned m, double v) { return __shfl_down_sync(m, v, 1); }
+__device__ __forceinline__ float shfl_down1(unsigned m, float v) { return __shfl_down_sync(m, v, 1); }
+__device__ __forceinline__ unsigned short shfl_down1(unsigned m, unsigned short v) {
+    return (unsigned short)__shfl_down_sync(m, (unsigned)v, 1);
+}
 
 // VEC mask bytes of consecutive nodes, as one integer (node k in byte k).
 template <int VEC> __device__ __forceinline__ unsigned long long ld_mask(const uint8_t *p);
@@ -1044,10 +1056,11 @@ struct NodeRange {
     }
 };
 
-// Stores of the thread's VEC nodes for the three step kinds.
+// Stores of the thread's VEC nodes for the three step kinds.  actm: the
+// warp's lanes that store (all of them call this together); lane: this one.
 template <class S, class A, int MODE, bool HAS_MASK>
 __device__ __forceinline__ void store_all(const A &ad, typename S::R *dst, unsigned long long mv,
-                                           const V16<typename S::R, S::VEC> out[9]) {
+                                           const V16<typename S::R, S::VEC> out[9], unsigned actm, int lane) {
     typedef typename S::R R;
     constexpr int VEC = S::VEC;
     if constexpr (MODE == MODE_TWO_LATTICE) {
@@ -1062,20 +1075,70 @@ __device__ __forceinline__ void store_all(const A &ad, typename S::R *dst, unsig
         // slot opp(i) at x when x + c_i is solid or beyond a wall (link
         // opp(i) of x bounces).  Each target slot has exactly one writer.
         st16<R, VEC>(dst + ad.vidx(0, 0), out[0]);
+        // realigned stores without a mask, except FP16s on tiles, where one
+        // lane in four starts a tile row and its element-wise 2-byte stores
+        // cost more than they save (measured -2% on the tiled box)
+        if constexpr (!HAS_MASK && (sizeof(R) >= 4 || std::is_same<A, DenseAddr<VEC>>::value)) {
+            // no bounced link: the x-shifted targets of the thread's VEC
+            // nodes are realigned by shuffles, so that each thread stores the
+            // aligned vector x0 .. x0 + VEC - 1 of the target row (as the
+            // gather realigns its loads); a value whose target vector
+            // belongs to a lane outside the warp, the tile row or the
+            // storing lanes is stored on its own, and that lane stores its
+            // other elements one by one
+            const bool lin = lane > 0 && ad.left_in_warp(lane) && ((actm >> (lane - 1)) & 1u);
+            const bool rin = lane < 31 && ad.right_in_warp(lane) && ((actm >> (lane + 1)) & 1u);
+            __syncwarp(actm);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            const unsigned long long rep = mask_rep<VEC>(opp(i) - 1);
-            if (cx(i) == 0 && (!HAS_MASK || (mv & rep) == 0ull)) {
-                st16<R, VEC>(dst + ad.vidx(i, cy(i)), out[i]);
-            } else {
+            for (int i = 1; i < 9; ++i) {
+                if (cx(i) == 0) {
+                    st16<R, VEC>(dst + ad.vidx(i, cy(i)), out[i]);
+                } else if (cx(i) == 1) {
+                    // target x + 1: element k of this vector is node k - 1's
+                    const R l = shfl_up1(actm, out[i].v[VEC - 1]);
+                    if (lin) {
+                        V16<R, VEC> v;
+                        v.v[0] = l;
 #pragma unroll
-                for (int k = 0; k < VEC; ++k) {
-                    const unsigned m = HAS_MASK ? (unsigned)((mv >> (8 * k)) & 0xFFu) : 0u;
-                    if (m == 0xFFu) continue;
-                    if (m & (1u << (opp(i) - 1)))
-                        dst[ad.eidx(opp(i), k, 0, 0)] = out[i].v[k];
-                    else
-                        dst[ad.eidx(i, k, cx(i), cy(i))] = out[i].v[k];
+                        for (int k = 1; k < VEC; ++k) v.v[k] = out[i].v[k - 1];
+                        st16<R, VEC>(dst + ad.vidx(i, cy(i)), v);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < VEC - 1; ++k) dst[ad.eidx(i, k, 1, cy(i))] = out[i].v[k];
+                    }
+                    if (!rin) dst[ad.eidx(i, VEC - 1, 1, cy(i))] = out[i].v[VEC - 1];
+                } else {
+                    // target x - 1: element k of this vector is node k + 1's
+                    const R r = shfl_down1(actm, out[i].v[0]);
+                    if (rin) {
+                        V16<R, VEC> v;
+#pragma unroll
+                        for (int k = 0; k < VEC - 1; ++k) v.v[k] = out[i].v[k + 1];
+                        v.v[VEC - 1] = r;
+                        st16<R, VEC>(dst + ad.vidx(i, cy(i)), v);
+                    } else {
+#pragma unroll
+                        for (int k = 1; k < VEC; ++k) dst[ad.eidx(i, k, -1, cy(i))] = out[i].v[k];
+                    }
+                    if (!lin) dst[ad.eidx(i, 0, -1, cy(i))] = out[i].v[0];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const unsigned long long rep = mask_rep<VEC>(opp(i) - 1);
+                if (cx(i) == 0 && (!HAS_MASK || (mv & rep) == 0ull)) {
+                    st16<R, VEC>(dst + ad.vidx(i, cy(i)), out[i]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        const unsigned m = HAS_MASK ? (unsigned)((mv >> (8 * k)) & 0xFFu) : 0u;
+                        if (m == 0xFFu) continue;
+                        if (m & (1u << (opp(i) - 1)))
+                            dst[ad.eidx(opp(i), k, 0, 0)] = out[i].v[k];
+                        else
+                            dst[ad.eidx(i, k, cx(i), cy(i))] = out[i].v[k];
+                    }
                 }
             }
         }
@@ -1118,12 +1181,14 @@ __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const 
     // written whole (its solid nodes hold 0 and get 0): there the gather
     // need not wait for the mask
     const bool active = ad.valid && (A::LIST_ || !(HAS_MASK && mv == mask_ones<VEC>()));
-    if (!__any_sync(LBM_FULL, active)) return; // whole warp solid: no traffic
+    const unsigned actm = __ballot_sync(LBM_FULL, active);
+    if (actm == 0u) return; // whole warp solid: no traffic
 
     V16<R, VEC> raw[9];
     R edge[9];
     gather_raw<S, MODE>(ad, src, active, lane, mv, raw, edge);
-    if (!active) return; // no collective operation follows
+    // the inactive lanes leave; the store's shuffles run among actm
+    if (!active) return;
     V16<R, VEC> own[9];
     if (HAS_MASK && MODE != MODE_AA_LOCAL && OwnPreload<S, MODE>::value && mv != 0ull)
         preload_own<S, MODE>(ad, src, mv, own);
@@ -1141,7 +1206,7 @@ __device__ __forceinline__ void step_vector(const Geo &g, const Phys &ph, const 
     }
     NodeRange<S, A, MODE, HAS_MASK, FORCE, OPEN, 0, VEC, TRT>::run(g, ph, ad, src, own, mv, raw, edge, Fx, Fy, co, sr,
                                                                    out);
-    store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out);
+    store_all<S, A, MODE, HAS_MASK>(ad, dst, mv, out, actm, lane);
 }
 
 // Whether the step over the list of fluid vectors runs as a persistent grid:
