@@ -21,8 +21,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "_build", "liblbm_oracle.so")
-_SOURCES = ["lbm_oracle.c", "lbm_oracle_cs.c"]
-_DEPS = _SOURCES + ["lbm_oracle.h", "lattice.inc", "step_body.inc"]
+_SOURCES = ["lbm_oracle.c", "lbm_oracle_cs.c", "lbm3_oracle.c"]
+_DEPS = _SOURCES + ["lbm_oracle.h", "lbm3_oracle.h", "lattice.inc", "step_body.inc"]
 
 SOLID = 0xFF
 
