@@ -638,10 +638,35 @@ def extra_measurements(args):
                     alu["note"] = "FP64 instructions per node of the dense step (a lower bound for this step)"
                     out[key]["alu_roofline"] = alu
         out["porous_phi%.2f_%d/fluid_nodes" % (achieved, n)] = nf
+    out["d3q19_taylor_green_256"] = d3q19_rows(peak, stream)
     # eta_P of the paper's two sparse geometries (Sec. 4.2.2) at three porosities
     out["eta_P_sweep"] = porosity_sweep(n, 300, names=("random_r8_256", "array_8x8"), phis=(0.3, 0.5, 0.8))
     out["adjoint_channel_512x256"] = adjoint_cost()
     return out
+
+
+def d3q19_rows(peak: float, stream, n: int = 256):
+    """The D3Q19 step (lbm3_*) on an n^3 periodic 3-D Taylor-Green box
+    (U 0.05, tau 0.8): GLUPS and the fraction of the 2 x 19 x s bytes per
+    node (152 B FP32, 304 B FP64) at the measured HBM peak."""
+    import torch
+    from paper_2108_13241_gb300 import inputs, lbm
+    rho, u = inputs.taylor_green_3d(n, n, n, 0.05)
+    rows = {}
+    for prec, k in (("f32", 200), ("f64", 50)):
+        sim = lbm.LBM3(n, n, n, 0.8, precision=prec)
+        sim.init_equilibrium(rho, u)
+        t = time_steps(sim, k, 10, stream)
+        _, v = sim.macros()
+        finite = bool(torch.isfinite(v).all())
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        g = n ** 3 * k / t / 1e9
+        nb = 2 * 19 * BYTES_PER_VALUE[prec]
+        rows[prec] = {"GLUPS": round(g, 3), "bytes_per_node": nb, "GBps_algorithmic": round(g * nb, 1),
+                      "frac_of_measured_hbm": round(g * nb / peak, 4), "steps": k, "finite": finite}
+    return rows
 
 
 def porosity_sweep(n: int = 4096, steps: int = 300, names=None, phis=None):
@@ -871,8 +896,18 @@ def main():
                     help="run the paper's two channel flows (4096 x 512, 10^6 steps) instead of the benchmark")
     ap.add_argument("--adjoint", action="store_true",
                     help="run the adjoint cost on the 512 x 256 channel and on a 2048 x 2048 one")
+    ap.add_argument("--d3q19", action="store_true",
+                    help="run the D3Q19 step on an n^3 3-D Taylor-Green box (n = --n, default 256 here)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.d3q19:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        n = 256 if args.n == 4096 else args.n
+        res = {"sweep": "d3q19", "n": n, "results": d3q19_rows(peaks()[0], torch.cuda.current_stream(), n)}
+        print(json.dumps(res), flush=True)
+        return 0
     if args.sweep or args.porosity_sweep or args.channels or args.adjoint:
         import __graft_entry__
         __graft_entry__.build()

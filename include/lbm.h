@@ -337,6 +337,63 @@ long long lbm_step_launches(const lbm_ctx *ctx, int n);
 const char *lbm_status_string(lbm_status s);
 const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Three-dimensional D3Q19 step (lbm3_*): Algorithm 1 carried to three
+ * dimensions, the extension the paper names as future work (Sec. 5).  The
+ * moments (Eq. 2 with the Guo F/2 shift), the BGK relaxation (Eq. 3-5) and
+ * the equilibrium (Eq. 6, with the D3Q19 weights 1/3 rest, 1/18 axis, 1/36
+ * diagonal) are the two-dimensional step's; dense storage, two lattices,
+ * stationary half-way bounce-back walls and obstacles, uniform body force.
+ *  Lattice: i = 0 rest; 1 (+1,0,0), 2 (-1,0,0), 3 (0,+1,0), 4 (0,-1,0),
+ *  5 (0,0,+1), 6 (0,0,-1); 7 (+1,+1,0), 8 (-1,-1,0), 9 (+1,-1,0),
+ *  10 (-1,+1,0); 11 (+1,0,+1), 12 (-1,0,-1), 13 (+1,0,-1), 14 (-1,0,+1);
+ *  15 (0,+1,+1), 16 (0,-1,-1), 17 (0,+1,-1), 18 (0,-1,+1) -- links 2k-1 and
+ *  2k are opposite.
+ *  Node (x, y, z) has index n = (z*ny + y)*nx + x.  Canonical device arrays
+ *  (compute type: double for LBM_F64, float for LBM_F32): distributions
+ *  f[19][nz][ny][nx] (the post-collision state A_t, solid nodes read w_i),
+ *  vector fields v[3][nz][ny][nx], scalar fields s[nz][ny][nx].  Device
+ *  pointers 16-byte aligned; ownership, streams and errors as above (the
+ *  workspace is the caller's, 256-byte aligned; calls are asynchronous on
+ *  params.stream except lbm3_create, which synchronises; a CUDA error is
+ *  sticky). */
+typedef struct lbm3_ctx lbm3_ctx;
+typedef struct {
+    int nx, ny, nz;              /* ny, nz <= 65535; 19*nx*ny*nz < 2^32 */
+    const uint8_t *solid;        /* host [nz][ny][nx], 1 = solid; NULL = all fluid; read at create */
+    double tau;                  /* > 0.5 (omega = 1/tau, Eq. 5) */
+    double fx, fy, fz;           /* uniform body-force density (Guo) */
+    int periodic_x, periodic_y, periodic_z; /* 0: stationary half-way bounce-back walls on both faces */
+    lbm_precision precision;     /* LBM_F64 or LBM_F32 */
+    void *stream;                /* cudaStream_t; NULL = legacy default stream */
+} lbm3_params;
+
+/* Workspace bytes for p: two lattices (19 values a node) and, when some link
+ * bounces, a 32-bit link mask per node.  Pure host; LBM_ERR_INVALID for bad
+ * parameters. */
+lbm_status lbm3_workspace_bytes(const lbm3_params *p, size_t *bytes);
+/* Builds the link mask on the host (bit i-1: link i pulls from a solid node
+ * or across a wall face), carves the lattices and the mask out of
+ * d_workspace (256-byte aligned, at least lbm3_workspace_bytes), zeroes the
+ * lattices (every node at rest, rho = 1) and synchronises.  LBM_ERR_OOM when
+ * the workspace is too small. */
+lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lbm3_ctx **out);
+/* Frees the context's host memory (the workspace stays the caller's). */
+lbm_status lbm3_destroy(lbm3_ctx *ctx);
+/* A_0 = f^eq(rho, u) (Algorithm 1, initialisation); NULL rho: 1, NULL u: 0. */
+lbm_status lbm3_init_equilibrium(lbm3_ctx *ctx, const void *d_rho, const void *d_u);
+/* n fused pull stream-and-collide steps (Algorithm 1), one launch each. */
+lbm_status lbm3_step(lbm3_ctx *ctx, int n);
+/* rho and u = (sum c f' + F/2)/rho at the current time (Eq. 2), 0 at solid
+ * nodes; either pointer may be NULL. */
+lbm_status lbm3_macros(lbm3_ctx *ctx, void *d_rho, void *d_u);
+/* Canonical state out / in (checkpoints, tests). */
+lbm_status lbm3_get_f(lbm3_ctx *ctx, void *d_f);
+lbm_status lbm3_set_f(lbm3_ctx *ctx, const void *d_f);
+long long lbm3_fluid_nodes(const lbm3_ctx *ctx);
+long long lbm3_step_count(const lbm3_ctx *ctx);
+const char *lbm3_last_error(const lbm3_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

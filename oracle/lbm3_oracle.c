@@ -151,6 +151,9 @@ void orc3_step(const orc3_params *p, const uint32_t *mask, const double *A, doub
     const long N = (long)p->nx * p->ny * p->nz;
     const double om = 1.0 / p->tau;
     const double F[3] = {p->fx, p->fy, p->fz};
+    /* the planes are independent: OpenMP splits them over threads, each
+     * node's arithmetic is the same whatever the thread count */
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -186,6 +189,7 @@ void orc3_run(const orc3_params *p, const uint32_t *mask, double *A, double *B, 
 void orc3_macros(const orc3_params *p, const uint32_t *mask, const double *A, double *rho, double *u)
 {
     const long N = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {

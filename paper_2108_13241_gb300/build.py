@@ -23,7 +23,7 @@ LIB = os.path.join(LIBDIR, "liblbm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["lbm_api.cu", "kern_f64.cu", "kern_f32.cu", "kern_f16s.cu", "kern_f64_trt.cu", "kern_f32_trt.cu",
-                "kern_f16s_trt.cu", "lbm_noalloc.cu"]
+                "kern_f16s_trt.cu", "lbm_noalloc.cu", "lbm3.cu"]
 CXX_SOURCES = ["lbm_geometry.cpp"]
 HEADERS = ["lbm_internal.h", "lbm_kernels.cuh", "lbm_staged.cuh"]
 

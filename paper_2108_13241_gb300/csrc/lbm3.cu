@@ -1,0 +1,521 @@
+// lbm3.cu -- the D3Q19 stream-and-collide step (Algorithm 1 of the paper in
+// three dimensions, the extension named as future work in Sec. 5) and its
+// C-ABI entry points (lbm3_* in include/lbm.h).
+//
+// Dense SoA storage f[i][z][y][x] of the shifted values f_i - w_i (FP64 or
+// FP32), two lattices swapped by pointer.  One node per thread: the 19 pulls
+// f'_i(x) = A_i(x - c_i) are 19 loads whose lanes read consecutive nodes of
+// one (slot, row) -- coalesced, the x-shifted ones one 32-byte sector wider
+// -- and the 19 stores are aligned.  Bounced links (a solid source or a wall
+// face, one bit each in a per-node 32-bit link mask) read the node's own
+// value of the opposite link (half-way bounce-back).  The collision is BGK
+// (Eq. 3-5) toward Eq. 6 with the D3Q19 weights plus the Guo source,
+// regrouped per pair of opposite links into an even part and an odd part
+// (exact algebra, fewer operations).  The register footprint stays small
+// (19 values a thread), the concern the paper raises for three dimensions.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+
+namespace {
+
+constexpr int Q3 = 19;
+constexpr uint32_t SOLID3 = 0xFFFFFFFFu;
+constexpr int BLOCK3 = 128;
+
+// Velocities (the order of lbm.h): rest; +-x, +-y, +-z; the xy, xz and yz
+// edge diagonals, opposite links adjacent (2k - 1, 2k).
+__host__ __device__ constexpr int c3(int i, int a) {
+    constexpr int t[Q3][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                              {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                              {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][a];
+}
+__host__ __device__ constexpr int opp3(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+template <class T> __host__ __device__ constexpr T w3(int i) {
+    return i == 0 ? T(1.0 / 3.0) : (i <= 6 ? T(1.0 / 18.0) : T(1.0 / 36.0));
+}
+
+struct Geo3 {
+    int nx, ny, nz;
+    int px, py, pz;        // periodic axes
+    unsigned N;            // nodes (19 N < 2^32, checked at create)
+    const uint32_t *mask;  // [nz][ny][nx]; NULL: every node fluid, all axes periodic
+};
+struct Phys3 {
+    double om, kk, fx, fy, fz; // omega = 1/tau, 1 - omega/2, force
+    float om_f, kk_f, fx_f, fy_f, fz_f;
+};
+template <class T> struct P3;
+template <> struct P3<double> {
+    static __device__ __forceinline__ double om(const Phys3 &p) { return p.om; }
+    static __device__ __forceinline__ double kk(const Phys3 &p) { return p.kk; }
+    static __device__ __forceinline__ void F(const Phys3 &p, double &x, double &y, double &z) {
+        x = p.fx; y = p.fy; z = p.fz;
+    }
+};
+template <> struct P3<float> {
+    static __device__ __forceinline__ float om(const Phys3 &p) { return p.om_f; }
+    static __device__ __forceinline__ float kk(const Phys3 &p) { return p.kk_f; }
+    static __device__ __forceinline__ void F(const Phys3 &p, float &x, float &y, float &z) {
+        x = p.fx_f; y = p.fy_f; z = p.fz_f;
+    }
+};
+
+// The node a thread updates, and its neighbours' coordinates along each
+// axis (periodic: wrapped; wall: clamped -- those links bounce and their
+// address is never used).
+struct Node3 {
+    int x, y, z;
+    unsigned n;
+    int xs[3], ys[3], zs[3]; // coordinate - 1, itself, + 1
+    __device__ __forceinline__ Node3(const Geo3 &g, int x_, int y_, int z_) : x(x_), y(y_), z(z_) {
+        n = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
+        nb(x, g.nx, g.px, xs);
+        nb(y, g.ny, g.py, ys);
+        nb(z, g.nz, g.pz, zs);
+    }
+    static __device__ __forceinline__ void nb(int c, int n, int per, int o[3]) {
+        o[0] = c > 0 ? c - 1 : (per ? n - 1 : 0);
+        o[1] = c;
+        o[2] = c < n - 1 ? c + 1 : (per ? 0 : n - 1);
+    }
+    // node index of the pull source x - c_i
+    __device__ __forceinline__ unsigned src(const Geo3 &g, int i) const {
+        const int sx = xs[1 - c3(i, 0)], sy = ys[1 - c3(i, 1)], sz = zs[1 - c3(i, 2)];
+        return ((unsigned)sz * (unsigned)g.ny + (unsigned)sy) * (unsigned)g.nx + (unsigned)sx;
+    }
+};
+
+// The gather of Algorithm 1 for one node: f'_i = A_i(x - c_i), or the
+// node's own value of the opposite link where link i bounces (bit i - 1).
+template <class T, bool HM>
+__device__ __forceinline__ void gather3(const Geo3 &g, const Node3 &nd, const T *A, uint32_t m, T f[Q3]) {
+    f[0] = A[nd.n];
+#pragma unroll
+    for (int i = 1; i < Q3; ++i) {
+        if (HM && (m & (1u << (i - 1)))) f[i] = A[(unsigned)opp3(i) * g.N + nd.n];
+        else f[i] = A[(unsigned)i * g.N + nd.src(g, i)];
+    }
+}
+
+// Moments of the shifted f' (Eq. 2 with the Guo shift): drho = rho - 1,
+// j = rho u = sum c f' + F/2.
+template <class T>
+__device__ __forceinline__ void moments3(const T f[Q3], T Fx, T Fy, T Fz, T &drho, T &jx, T &jy, T &jz) {
+    drho = T(0);
+    jx = jy = jz = T(0);
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) {
+        drho += f[i];
+        if (c3(i, 0)) jx += c3(i, 0) > 0 ? f[i] : -f[i];
+        if (c3(i, 1)) jy += c3(i, 1) > 0 ? f[i] : -f[i];
+        if (c3(i, 2)) jz += c3(i, 2) > 0 ? f[i] : -f[i];
+    }
+    jx += T(0.5) * Fx;
+    jy += T(0.5) * Fy;
+    jz += T(0.5) * Fz;
+}
+
+// BGK relaxation toward Eq. 6 plus the Guo source, on shifted values:
+//   f_i <- (1 - omega) f_i + omega (f^eq_i - w_i) + S_i,
+//   f^eq_i - w_i = w_i [drho + rho (3 t + 4.5 t^2 - 1.5 u.u)], t = c_i . u,
+//   S_i = (1 - omega/2) w_i [3 (c_i . F) - 3 u.F + 9 t (c_i . F)],
+// taken per pair (i, opp(i)) as the even part E (the same for both) and the
+// odd part O = 3 w_i [omega (c_i . j) + (1 - omega/2) (c_i . F)] (+ for i,
+// - for opp(i)).
+template <class T, bool HAS_F>
+__device__ __forceinline__ void collide3(T f[Q3], T om, T kk, T Fx, T Fy, T Fz) {
+    T drho, jx, jy, jz;
+    moments3<T>(f, Fx, Fy, Fz, drho, jx, jy, jz);
+    const T rho = T(1) + drho;
+    const T inv = T(1) / rho;
+    const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const T usq = T(1.5) * (ux * ux + uy * uy + uz * uz);
+    const T uF = HAS_F ? ux * Fx + uy * Fy + uz * Fz : T(0);
+    const T om1 = T(1) - om;
+    const T base = drho - rho * usq;
+    {
+        T e = om * base;
+        if (HAS_F) e -= kk * T(3) * uF;
+        f[0] = om1 * f[0] + w3<T>(0) * e;
+    }
+#pragma unroll
+    for (int i = 1; i < Q3; i += 2) {
+        const T cx = T(c3(i, 0)), cy = T(c3(i, 1)), cz = T(c3(i, 2));
+        const T t = cx * ux + cy * uy + cz * uz;
+        const T cj = cx * jx + cy * jy + cz * jz;
+        T e = om * (base + T(4.5) * rho * t * t);
+        T o = om * cj;
+        if (HAS_F) {
+            const T cF = cx * Fx + cy * Fy + cz * Fz;
+            e += kk * (T(9) * t * cF - T(3) * uF);
+            o += kk * cF;
+        }
+        e *= w3<T>(i);
+        o *= T(3) * w3<T>(i);
+        f[i] = om1 * f[i] + (e + o);
+        f[i + 1] = om1 * f[i + 1] + (e - o);
+    }
+}
+
+template <class T, bool HM, bool HAS_F>
+__global__ void __launch_bounds__(BLOCK3) k3_step(const Geo3 g, const Phys3 ph, const T *__restrict__ A,
+                                                  T *__restrict__ B) {
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= g.nx) return;
+    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
+    uint32_t m = 0u;
+    if (HM) {
+        m = g.mask[nd.n];
+        if (m == SOLID3) return; // never read: nothing to store
+    }
+    T f[Q3];
+    gather3<T, HM>(g, nd, A, m, f);
+    T Fx, Fy, Fz;
+    P3<T>::F(ph, Fx, Fy, Fz);
+    collide3<T, HAS_F>(f, P3<T>::om(ph), P3<T>::kk(ph), Fx, Fy, Fz);
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) B[(unsigned)i * g.N + nd.n] = f[i];
+}
+
+// rho and u at the current time (the gather without the collision); 0 at
+// solid nodes.
+template <class T>
+__global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph, const T *A, T *rho, T *u) {
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= g.nx) return;
+    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
+    const uint32_t m = g.mask ? g.mask[nd.n] : 0u;
+    if (m == SOLID3) {
+        if (rho) rho[nd.n] = T(0);
+        if (u)
+            for (int a = 0; a < 3; ++a) u[(unsigned)a * g.N + nd.n] = T(0);
+        return;
+    }
+    T f[Q3];
+    if (g.mask) gather3<T, true>(g, nd, A, m, f);
+    else gather3<T, false>(g, nd, A, m, f);
+    T Fx, Fy, Fz, drho, jx, jy, jz;
+    P3<T>::F(ph, Fx, Fy, Fz);
+    moments3<T>(f, Fx, Fy, Fz, drho, jx, jy, jz);
+    const T r = T(1) + drho;
+    if (rho) rho[nd.n] = r;
+    if (u) {
+        u[nd.n] = jx / r;
+        u[g.N + nd.n] = jy / r;
+        u[2u * g.N + nd.n] = jz / r;
+    }
+}
+
+// A = f^eq(rho, u) - w at fluid nodes (rho = 1, u = 0 where NULL), 0 (that
+// is, w) at solid nodes.
+template <class T>
+__global__ void __launch_bounds__(BLOCK3) k3_init(const Geo3 g, const T *rho, const T *u, T *A) {
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= g.nx) return;
+    const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
+    const bool solid = g.mask && g.mask[n] == SOLID3;
+    const T r = rho ? rho[n] : T(1);
+    const T ux = u ? u[n] : T(0), uy = u ? u[g.N + n] : T(0), uz = u ? u[2u * g.N + n] : T(0);
+    const T usq = T(1.5) * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) {
+        const T t = T(c3(i, 0)) * ux + T(c3(i, 1)) * uy + T(c3(i, 2)) * uz;
+        const T d = w3<T>(i) * ((r - T(1)) + r * (T(3) * t + T(4.5) * t * t - usq));
+        A[(unsigned)i * g.N + n] = solid ? T(0) : d;
+    }
+}
+
+// canonical f = stored + w (get), stored = f - w (set)
+template <class T>
+__global__ void __launch_bounds__(BLOCK3) k3_convert(const Geo3 g, const T *in, T *out, int to_canonical) {
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= g.nx) return;
+    const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) {
+        const unsigned k = (unsigned)i * g.N + n;
+        out[k] = to_canonical ? in[k] + w3<T>(i) : in[k] - w3<T>(i);
+    }
+}
+
+} // namespace
+
+// ------------------------------------------------------------- C ABI
+
+struct lbm3_ctx {
+    lbm3_params p;
+    Geo3 g;
+    Phys3 ph;
+    size_t es = 0;   // bytes per stored value
+    void *lat[2] = {nullptr, nullptr};
+    int cur = 0;     // lattice holding A_t
+    long long steps = 0, nfluid = 0;
+    cudaStream_t stream = nullptr;
+    lbm_status sticky = LBM_OK;
+    std::string err;
+};
+
+namespace {
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+const char *check3(const lbm3_params *p) {
+    if (!p) return "params is NULL";
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
+    if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
+    if ((double)Q3 * p->nx * p->ny * p->nz >= 4294967296.0) return "19*nx*ny*nz must be < 2^32";
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be > 0.5";
+    if (!std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->fz)) return "force must be finite";
+    if (p->precision != LBM_F64 && p->precision != LBM_F32) return "precision must be LBM_F64 or LBM_F32";
+    return nullptr;
+}
+
+// Link mask (host): bit i - 1 set iff link i of a fluid node pulls from a
+// solid node or from beyond a wall face; SOLID3 for solid nodes.  Returns
+// the fluid node count; `any` tells whether some link bounces.
+long long build_mask3(const lbm3_params &p, std::vector<uint32_t> &m, bool &any) {
+    const long long N = (long long)p.nx * p.ny * p.nz;
+    m.assign((size_t)N, 0u);
+    any = false;
+    long long nf = 0;
+    const int n[3] = {p.nx, p.ny, p.nz};
+    const int per[3] = {p.periodic_x != 0, p.periodic_y != 0, p.periodic_z != 0};
+    for (int z = 0; z < p.nz; ++z)
+        for (int y = 0; y < p.ny; ++y)
+            for (int x = 0; x < p.nx; ++x) {
+                const long long k = ((long long)z * p.ny + y) * p.nx + x;
+                if (p.solid && p.solid[k]) {
+                    m[(size_t)k] = SOLID3;
+                    any = true;
+                    continue;
+                }
+                ++nf;
+                uint32_t bits = 0;
+                for (int i = 1; i < Q3; ++i) {
+                    int q[3] = {x - c3(i, 0), y - c3(i, 1), z - c3(i, 2)};
+                    bool out = false;
+                    for (int a = 0; a < 3; ++a)
+                        if (q[a] < 0 || q[a] >= n[a]) {
+                            if (per[a]) q[a] = (q[a] + n[a]) % n[a];
+                            else out = true;
+                        }
+                    if (out || (p.solid && p.solid[((long long)q[2] * p.ny + q[1]) * p.nx + q[0]]))
+                        bits |= 1u << (i - 1);
+                }
+                m[(size_t)k] = bits;
+                any = any || bits != 0u;
+            }
+    return nf;
+}
+
+struct Plan3 {
+    size_t lat, off1, offm, total;
+    bool has_mask;
+};
+Plan3 plan3(const lbm3_params &p, bool has_mask) {
+    Plan3 pl;
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
+    const size_t es = p.precision == LBM_F64 ? 8 : 4;
+    pl.lat = Q3 * N * es;
+    pl.off1 = al256(pl.lat);
+    pl.offm = pl.off1 + al256(pl.lat);
+    pl.has_mask = has_mask;
+    pl.total = pl.offm + (has_mask ? al256(N * 4) : 0);
+    return pl;
+}
+bool any_bounce(const lbm3_params &p) {
+    if (!p.periodic_x || !p.periodic_y || !p.periodic_z) return true;
+    if (p.solid) {
+        const size_t N = (size_t)p.nx * p.ny * p.nz;
+        for (size_t k = 0; k < N; ++k)
+            if (p.solid[k]) return true;
+    }
+    return false;
+}
+
+lbm_status fail3(lbm3_ctx *c, lbm_status s, const std::string &msg) {
+    if (c) {
+        if (s == LBM_ERR_CUDA) c->sticky = s;
+        c->err = msg;
+    }
+    return s;
+}
+lbm_status cuda3(lbm3_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LBM_OK;
+    return fail3(c, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+dim3 grid3(const Geo3 &g) {
+    return dim3((unsigned)((g.nx + BLOCK3 - 1) / BLOCK3), (unsigned)g.ny, (unsigned)g.nz);
+}
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <class T> cudaError_t step3(lbm3_ctx *c) {
+    const T *A = static_cast<const T *>(c->lat[c->cur]);
+    T *B = static_cast<T *>(c->lat[1 - c->cur]);
+    const bool F = c->p.fx != 0.0 || c->p.fy != 0.0 || c->p.fz != 0.0;
+    const dim3 gr = grid3(c->g);
+    if (c->g.mask) {
+        if (F) k3_step<T, true, true><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
+        else k3_step<T, true, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
+    } else {
+        if (F) k3_step<T, false, true><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
+        else k3_step<T, false, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
+    }
+    return cudaGetLastError();
+}
+
+} // namespace
+
+extern "C" {
+
+lbm_status lbm3_workspace_bytes(const lbm3_params *p, size_t *bytes) {
+    if (check3(p) || !bytes) return LBM_ERR_INVALID;
+    *bytes = plan3(*p, any_bounce(*p)).total;
+    return LBM_OK;
+}
+
+lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lbm3_ctx **out) {
+    if (!out) return LBM_ERR_INVALID;
+    *out = nullptr;
+    if (check3(p) || !d_workspace || ((uintptr_t)d_workspace & 255u)) return LBM_ERR_INVALID;
+    std::vector<uint32_t> mask;
+    bool any = false;
+    const long long nf = build_mask3(*p, mask, any);
+    const Plan3 pl = plan3(*p, any);
+    if (bytes < pl.total) return LBM_ERR_OOM;
+    lbm3_ctx *c = new lbm3_ctx();
+    c->p = *p;
+    c->p.solid = nullptr; // read here only
+    c->es = p->precision == LBM_F64 ? 8 : 4;
+    c->stream = static_cast<cudaStream_t>(p->stream);
+    c->nfluid = nf;
+    char *ws = static_cast<char *>(d_workspace);
+    c->lat[0] = ws;
+    c->lat[1] = ws + pl.off1;
+    Geo3 &g = c->g;
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.nz = p->nz;
+    g.px = p->periodic_x != 0;
+    g.py = p->periodic_y != 0;
+    g.pz = p->periodic_z != 0;
+    g.N = (unsigned)((size_t)p->nx * p->ny * p->nz);
+    g.mask = any ? reinterpret_cast<const uint32_t *>(ws + pl.offm) : nullptr;
+    Phys3 &ph = c->ph;
+    ph.om = 1.0 / p->tau;
+    ph.kk = 1.0 - 0.5 * ph.om;
+    ph.fx = p->fx;
+    ph.fy = p->fy;
+    ph.fz = p->fz;
+    ph.om_f = (float)ph.om;
+    ph.kk_f = 1.0f - 0.5f * ph.om_f;
+    ph.fx_f = (float)p->fx;
+    ph.fy_f = (float)p->fy;
+    ph.fz_f = (float)p->fz;
+    lbm_status st = cuda3(c, cudaMemsetAsync(ws, 0, pl.offm, c->stream), "memset lattices");
+    if (!st && any)
+        st = cuda3(c, cudaMemcpyAsync(ws + pl.offm, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice, c->stream),
+                   "copy link mask");
+    if (!st) st = cuda3(c, cudaStreamSynchronize(c->stream), "create sync");
+    if (st) {
+        delete c;
+        return st;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm3_destroy(lbm3_ctx *ctx) {
+    if (!ctx) return LBM_ERR_INVALID;
+    delete ctx;
+    return LBM_OK;
+}
+
+#define LBM3_CHECK(ctx)                                   \
+    do {                                                  \
+        if (!(ctx)) return LBM_ERR_INVALID;               \
+        if ((ctx)->sticky != LBM_OK) return (ctx)->sticky; \
+    } while (0)
+
+lbm_status lbm3_init_equilibrium(lbm3_ctx *ctx, const void *d_rho, const void *d_u) {
+    LBM3_CHECK(ctx);
+    if ((d_rho && !aligned16(d_rho)) || (d_u && !aligned16(d_u)))
+        return fail3(ctx, LBM_ERR_INVALID, "fields must be 16-byte aligned");
+    const dim3 gr = grid3(ctx->g);
+    if (ctx->es == 8)
+        k3_init<double><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const double *>(d_rho),
+                                                         static_cast<const double *>(d_u),
+                                                         static_cast<double *>(ctx->lat[0]));
+    else
+        k3_init<float><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const float *>(d_rho),
+                                                       static_cast<const float *>(d_u),
+                                                       static_cast<float *>(ctx->lat[0]));
+    ctx->cur = 0;
+    ctx->steps = 0;
+    return cuda3(ctx, cudaGetLastError(), "init launch");
+}
+
+lbm_status lbm3_step(lbm3_ctx *ctx, int n) {
+    LBM3_CHECK(ctx);
+    if (n < 0) return fail3(ctx, LBM_ERR_INVALID, "n < 0");
+    for (int k = 0; k < n; ++k) {
+        const cudaError_t e = ctx->es == 8 ? step3<double>(ctx) : step3<float>(ctx);
+        if (e != cudaSuccess) return cuda3(ctx, e, "step launch");
+        ctx->cur = 1 - ctx->cur;
+        ++ctx->steps;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm3_macros(lbm3_ctx *ctx, void *d_rho, void *d_u) {
+    LBM3_CHECK(ctx);
+    if ((d_rho && !aligned16(d_rho)) || (d_u && !aligned16(d_u)))
+        return fail3(ctx, LBM_ERR_INVALID, "fields must be 16-byte aligned");
+    const dim3 gr = grid3(ctx->g);
+    if (ctx->es == 8)
+        k3_macros<double><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->ph,
+                                                           static_cast<const double *>(ctx->lat[ctx->cur]),
+                                                           static_cast<double *>(d_rho), static_cast<double *>(d_u));
+    else
+        k3_macros<float><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->ph,
+                                                         static_cast<const float *>(ctx->lat[ctx->cur]),
+                                                         static_cast<float *>(d_rho), static_cast<float *>(d_u));
+    return cuda3(ctx, cudaGetLastError(), "macros launch");
+}
+
+static lbm_status convert3(lbm3_ctx *ctx, const void *in, void *out, int to_canonical) {
+    const dim3 gr = grid3(ctx->g);
+    if (ctx->es == 8)
+        k3_convert<double><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const double *>(in),
+                                                            static_cast<double *>(out), to_canonical);
+    else
+        k3_convert<float><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const float *>(in),
+                                                          static_cast<float *>(out), to_canonical);
+    return cuda3(ctx, cudaGetLastError(), "convert launch");
+}
+
+lbm_status lbm3_get_f(lbm3_ctx *ctx, void *d_f) {
+    LBM3_CHECK(ctx);
+    if (!d_f || !aligned16(d_f)) return fail3(ctx, LBM_ERR_INVALID, "f must be a 16-byte aligned pointer");
+    return convert3(ctx, ctx->lat[ctx->cur], d_f, 1);
+}
+
+lbm_status lbm3_set_f(lbm3_ctx *ctx, const void *d_f) {
+    LBM3_CHECK(ctx);
+    if (!d_f || !aligned16(d_f)) return fail3(ctx, LBM_ERR_INVALID, "f must be a 16-byte aligned pointer");
+    return convert3(ctx, d_f, ctx->lat[ctx->cur], 0);
+}
+
+long long lbm3_fluid_nodes(const lbm3_ctx *ctx) { return ctx ? ctx->nfluid : -1; }
+long long lbm3_step_count(const lbm3_ctx *ctx) { return ctx ? ctx->steps : -1; }
+const char *lbm3_last_error(const lbm3_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+} // extern "C"

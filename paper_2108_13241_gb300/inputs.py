@@ -265,3 +265,31 @@ def random_field(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     n = int(np.prod(shape))
     v = np.array([rng.next_u64() >> 11 for _ in range(n)], dtype=np.float64) * (1.0 / (1 << 53))
     return (2.0 * v - 1.0).reshape(shape) * scale
+
+
+def random_solid_3d(nx: int, ny: int, nz: int, fraction: float, seed: int) -> np.ndarray:
+    """Independent random solid nodes of a three-dimensional box, uint8
+    [nz, ny, nx] (SplitMix64; for small parity cases)."""
+    rng = SplitMix64(seed)
+    vals = np.array([rng.next_u64() >> 11 for _ in range(nx * ny * nz)], dtype=np.float64)
+    return (vals * (1.0 / (1 << 53)) < fraction).astype(np.uint8).reshape(nz, ny, nx)
+
+
+def taylor_green_3d(nx: int, ny: int, nz: int, U: float):
+    """Three-dimensional Taylor-Green vortex at t = 0 on node coordinates
+    (k = 2 pi / n per axis): u_x = U sin(kx x) cos(ky y) cos(kz z),
+    u_y = -U (kx/ky) cos(kx x) sin(ky y) cos(kz z), u_z = 0, and the
+    pressure-consistent density rho = 1 + 3 p with
+    p = (U^2 / 16) (cos 2 kx x + cos 2 ky y)(cos 2 kz z + 2) (c_s^2 = 1/3).
+    Returns (rho [nz, ny, nx], u [3, nz, ny, nx])."""
+    kx, ky, kz = 2 * math.pi / nx, 2 * math.pi / ny, 2 * math.pi / nz
+    z = np.arange(nz)[:, None, None]
+    y = np.arange(ny)[None, :, None]
+    x = np.arange(nx)[None, None, :]
+    shape = (nz, ny, nx)
+    ux = np.broadcast_to(U * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z), shape)
+    uy = np.broadcast_to(-U * (kx / ky) * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z), shape)
+    uz = np.zeros(shape)
+    p = (U * U / 16.0) * (np.cos(2 * kx * x) + np.cos(2 * ky * y)) * (np.cos(2 * kz * z) + 2.0)
+    rho = np.broadcast_to(1.0 + 3.0 * p, shape).copy()
+    return rho, np.stack([ux, uy, uz])

@@ -65,6 +65,18 @@ class lbm_params(ctypes.Structure):
     ]
 
 
+class lbm3_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("solid", ctypes.c_void_p),
+        ("tau", ctypes.c_double),
+        ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("fz", ctypes.c_double),
+        ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int), ("periodic_z", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 _lib = None
 _P = ctypes.POINTER(lbm_params)
 _vp = ctypes.c_void_p
@@ -110,6 +122,17 @@ def _load():
         "lbm_step_launches": ([_vp, ctypes.c_int], ctypes.c_longlong),
         "lbm_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lbm_last_error": ([_vp], ctypes.c_char_p),
+        "lbm3_workspace_bytes": ([ctypes.POINTER(lbm3_params), ctypes.POINTER(ctypes.c_size_t)], st),
+        "lbm3_create": ([ctypes.POINTER(lbm3_params), _vp, ctypes.c_size_t, ctypes.POINTER(_vp)], st),
+        "lbm3_destroy": ([_vp], st),
+        "lbm3_init_equilibrium": ([_vp, _vp, _vp], st),
+        "lbm3_step": ([_vp, ctypes.c_int], st),
+        "lbm3_macros": ([_vp, _vp, _vp], st),
+        "lbm3_get_f": ([_vp, _vp], st),
+        "lbm3_set_f": ([_vp, _vp], st),
+        "lbm3_fluid_nodes": ([_vp], ctypes.c_longlong),
+        "lbm3_step_count": ([_vp], ctypes.c_longlong),
+        "lbm3_last_error": ([_vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -123,7 +146,7 @@ def header_symbols(path: str = HEADER) -> list:
     """Names of the functions include/lbm.h declares."""
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lbm3?_[a-z0-9_]+)\s*\(", text)))
 
 
 def _status_name(s: int) -> str:
@@ -562,3 +585,101 @@ class LBM:
         gr = None if g_rho is None else self._t(g_rho, (self.ny, self.nx))
         gu = None if g_u is None else self._t(g_u, (2, self.ny, self.nx))
         lbm_macros_backward(self.ctx, gr, gu, lam, grad_force)
+
+
+# ------------------------------------------------------------ D3Q19 (lbm3_*)
+
+def _check3(fn: str, status: int, ctx=None):
+    if status != LBM_OK:
+        detail = ""
+        if ctx:
+            detail = (_load().lbm3_last_error(ctx) or b"").decode()
+        raise LBMError(fn, status, detail)
+
+
+class LBM3:
+    """One D3Q19 context (lbm3_* of include/lbm.h) on the current CUDA device
+    and stream: dense, two lattices, stationary half-way bounce-back walls on
+    the faces of non-periodic axes and on solid nodes, uniform Guo force.
+    Canonical arrays: f [19, nz, ny, nx], u [3, nz, ny, nx], rho [nz, ny, nx]."""
+
+    def __init__(self, nx: int, ny: int, nz: int, tau: float, solid=None, force=(0.0, 0.0, 0.0),
+                 periodic=(True, True, True), precision="f32", device="cuda"):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        p = lbm3_params()
+        p.nx, p.ny, p.nz = self.nx, self.ny, self.nz
+        keep = None
+        if solid is not None:
+            keep = np.ascontiguousarray(solid, dtype=np.uint8)
+            assert keep.shape == (nz, ny, nx)
+            p.solid = keep.ctypes.data_as(ctypes.c_void_p)
+        p.tau = float(tau)
+        p.fx, p.fy, p.fz = (float(v) for v in force)
+        p.periodic_x, p.periodic_y, p.periodic_z = (int(bool(v)) for v in periodic)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.precision = prec
+        p.stream = torch.cuda.current_stream().cuda_stream or None
+        self.dtype = torch.float64 if prec == LBM_F64 else torch.float32
+        self.device = torch.device(device)
+        n = ctypes.c_size_t(0)
+        _check3("lbm3_workspace_bytes", _load().lbm3_workspace_bytes(ctypes.byref(p), ctypes.byref(n)))
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        ctx = ctypes.c_void_p()
+        _check3("lbm3_create", _load().lbm3_create(ctypes.byref(p), _ptr(self.workspace), self.workspace.numel(),
+                                                   ctypes.byref(ctx)))
+        self.ctx = ctx
+        del keep
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _load().lbm3_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def fluid_nodes(self) -> int:
+        return _load().lbm3_fluid_nodes(self.ctx)
+
+    @property
+    def steps(self) -> int:
+        return _load().lbm3_step_count(self.ctx)
+
+    def _t(self, t, shape):
+        t = torch.as_tensor(t, dtype=self.dtype, device=self.device).contiguous()
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError("expected shape %s, got %s" % (tuple(shape), tuple(t.shape)))
+        return t
+
+    def init_equilibrium(self, rho=None, u=None):
+        r = None if rho is None else self._t(rho, self.shape)
+        v = None if u is None else self._t(u, (3,) + self.shape)
+        _check3("lbm3_init_equilibrium", _load().lbm3_init_equilibrium(self.ctx, _ptr(r), _ptr(v)), self.ctx)
+        torch.cuda.current_stream().synchronize()
+
+    def step(self, n: int = 1):
+        _check3("lbm3_step", _load().lbm3_step(self.ctx, int(n)), self.ctx)
+
+    def macros(self):
+        rho = torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        u = torch.empty((3,) + self.shape, dtype=self.dtype, device=self.device)
+        _check3("lbm3_macros", _load().lbm3_macros(self.ctx, _ptr(rho), _ptr(u)), self.ctx)
+        return rho, u
+
+    def get_f(self) -> torch.Tensor:
+        f = torch.empty((19,) + self.shape, dtype=self.dtype, device=self.device)
+        _check3("lbm3_get_f", _load().lbm3_get_f(self.ctx, _ptr(f)), self.ctx)
+        return f
+
+    def set_f(self, f):
+        t = self._t(f, (19,) + self.shape)
+        _check3("lbm3_set_f", _load().lbm3_set_f(self.ctx, _ptr(t)), self.ctx)
+        torch.cuda.current_stream().synchronize()
