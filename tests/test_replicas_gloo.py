@@ -34,7 +34,9 @@ def _worker(rank, world, port, out):
 def test_two_gloo_ranks_take_the_slowest_time():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    # the manager process is spawned too: the oracle's OpenMP threads may
+    # already run in this process, and a fork after them can deadlock
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
