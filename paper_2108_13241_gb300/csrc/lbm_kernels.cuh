@@ -1695,6 +1695,63 @@ __global__ void __launch_bounds__(AUX_BLOCK) k_reduce_final(const double *partia
     block_sum4(acc, out);
 }
 
+// One adjoint step with one node per thread (dense two-lattice): the same
+// transpose as k_adjoint -- re-gather of f' from A_t in plain units
+// (gather_node), lambda_{t+1} at the node, adjoint_node, push of
+// g_j = dL/df'_j to slot j at x - c_j (slot opp(j) at x for a bounced link),
+// dL/dF accumulated -- with every access a scalar whose lanes touch
+// consecutive nodes of a row (coalesced; the x-shifted ones one sector
+// wider), no shuffles, and a small register footprint.
+template <int P, int FORCE, bool OPEN>
+__global__ void __launch_bounds__(STEP_BLOCK) k_adjoint1(const Geo g, const Phys ph, const void *state_v,
+                                                         const void *lam_in_v, void *lam_out_v, void *gF_v,
+                                                         int y0) {
+    typedef St<P> S;
+    typedef typename S::R R;
+    typedef typename S::C C;
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = y0 + (int)blockIdx.y;
+    if (x >= g.nx) return;
+    const long long n = (long long)y * g.nx + x;
+    const unsigned m = g.has_mask ? __ldg(g.mask + n) : 0u;
+    C *lout = reinterpret_cast<C *>(lam_out_v);
+    if (m == 0xFFu) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) lout[j * g.nnode + n] = C(0);
+        return;
+    }
+    const C *lin = reinterpret_cast<const C *>(lam_in_v);
+    C l[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) l[j] = __ldg(lin + j * g.nnode + n);
+    C f[9];
+    gather_node<S>(g, ph, PH_PLAIN, reinterpret_cast<const R *>(state_v), x, y, m, f);
+    if constexpr (OPEN) apply_open<C>(g, ph, x, y, m, f);
+    C Fx = PC<C>::fx(ph), Fy = PC<C>::fy(ph);
+    if constexpr (FORCE == FORCE_FIELD) {
+        const C *F = reinterpret_cast<const C *>(ph.force);
+        Fx = __ldg(F + n);
+        Fy = __ldg(F + g.nnode + n);
+    }
+    C gg[9], dFx, dFy;
+    adjoint_node<C, FORCE != FORCE_NONE>(f, l, Fx, Fy, PC<C>::omega(ph), gg, dFx, dFy);
+    if constexpr (OPEN) open_transpose<C>(g, ph, x, y, m, gg);
+    lout[n] = gg[0];
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+        if (m & (1u << (j - 1))) {
+            lout[opp(j) * g.nnode + n] = gg[j]; // bounced: the own node's opposite slot
+        } else {
+            int sx = x - cx(j), sy = y - cy(j);
+            wrap_xy(g, sx, sy);
+            lout[j * g.nnode + (long long)sy * g.nx + sx] = gg[j];
+        }
+    }
+    C *gF = reinterpret_cast<C *>(gF_v);
+    gF[n] += dFx;
+    gF[g.nnode + n] += dFy;
+}
+
 // Transpose of the macros at the current (two-lattice, dense) state.
 template <int P>
 __global__ void k_macros_adjoint(const Geo g, const Phys ph, const void *state_v, const void *grho_v,
@@ -1931,12 +1988,29 @@ cudaError_t launch_reduce(const Geo &g, const Phys &ph, int phase, int kind, con
     k_reduce_final<P><<<1, AUX_BLOCK, 0, s>>>(partial, RED_BLOCKS, out);
     return cudaGetLastError();
 }
+// The adjoint kernel: FP64 and FP32 take the vector kernel k_adjoint
+// (measured 4.99 against 3.99 TB/s for the one-node-per-thread kernel on a
+// 2048^2 channel); FP16s takes k_adjoint1, whose gather decodes the stored
+// values to plain units, as adjoint_node expects (the vector gather
+// decodes in the step's stored scale).  LBM_ADJ_SCALAR=1 sends every
+// precision to k_adjoint1.
+#ifndef LBM_ADJ_SCALAR
+#define LBM_ADJ_SCALAR 0
+#endif
 template <int P, int F, bool OPEN>
 static void adjoint_rows(const Geo &g, const Phys &ph, const void *state, const void *lam_in, void *lam_out,
                          void *grad_force, const Shape &sh, cudaStream_t s) {
-    for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
-        const dim3 grid(sh.gx, sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u);
-        k_adjoint<P, F, OPEN><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
+    if constexpr (LBM_ADJ_SCALAR != 0 || P == LBM_F16S) {
+        const unsigned gx = (unsigned)((g.nx + STEP_BLOCK - 1) / STEP_BLOCK);
+        for (unsigned y0 = 0; y0 < (unsigned)g.ny; y0 += 65535u) {
+            const dim3 grid(gx, (unsigned)g.ny - y0 < 65535u ? (unsigned)g.ny - y0 : 65535u);
+            k_adjoint1<P, F, OPEN><<<grid, STEP_BLOCK, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
+        }
+    } else {
+        for (unsigned y0 = 0; y0 < sh.rows; y0 += 65535u) {
+            const dim3 grid(sh.gx, sh.rows - y0 < 65535u ? sh.rows - y0 : 65535u);
+            k_adjoint<P, F, OPEN><<<grid, sh.bx, 0, s>>>(g, ph, state, lam_in, lam_out, grad_force, (int)y0);
+        }
     }
 }
 template <int P, int F>

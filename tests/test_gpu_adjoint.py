@@ -72,6 +72,23 @@ def test_adjoint_fp64_matches_oracle_chain(L, orc, T, K):
     assert np.all(g0[:, ~fl] == 0)
 
 
+def test_adjoint_fp16s_close_to_oracle_chain(L, orc):
+    """FP16-shifted storage, FP32 adjoint arithmetic: the gradients follow
+    the FP64 oracle's chain to within the storage's precision (binary16
+    keeps 11 bits, 4.9e-4 relative per stored value; the bound leaves ten
+    times that for the 24 steps' accumulation)."""
+    c = channel_case()
+    T, K = 24, 8
+    ut = inputs.target_velocity(c.nx, c.ny, c.solid, amp=0.02)
+    A0, lam, gF, mask, loss = oracle_grads(orc, c, T, ut)
+    g0, gFg, lg, _ = gpu_grads(L, c, T, K, ut, "f16s", A0)
+    fl = mask != 0xFF
+    assert abs(lg - loss) <= 1e-2 * abs(loss)
+    assert C.rel_l2(gFg, gF, fl) <= 5e-3
+    assert C.rel_l2(g0, lam, fl) <= 5e-3
+    assert np.all(g0[:, ~fl] == 0)
+
+
 def open_channel_case(nx=48, ny=32, seed=inputs.GEOMETRY_SEED + 3):
     """Velocity inlet west, pressure outlet east, walls in y, cylinders."""
     solid, _ = inputs.channel_cylinders(nx, ny, count=2, rmin=3, rmax=5, clearance=2, seed=seed)
