@@ -164,3 +164,30 @@ def test_arguments_are_checked(L):
         sim.step(-1)
     assert ei.value.status == L.LBM_ERR_INVALID
     sim.close()
+
+
+def test_benchmark_box_one_step_matches_oracle(L, o3):
+    """The benchmark's configuration (256^3 periodic 3-D Taylor-Green, FP32,
+    the launch bench.py times): one step from the GPU's own state after 10
+    steps, against the oracle's step from that state (FP32 storage rounding
+    only: 1e-6 relative L2 on f, 1e-5 on u)."""
+    n = 256
+    rho, u = inputs.taylor_green_3d(n, n, n, 0.05)
+    sim = L.LBM3(n, n, n, 0.8, precision="f32")
+    sim.init_equilibrium(rho, u)
+    del rho, u
+    sim.step(10)
+    A = sim.get_f().double().cpu().numpy()
+    sim.step(1)
+    f = sim.get_f().double().cpu().numpy()
+    _, v = sim.macros()
+    v = v.double().cpu().numpy()
+    sim.close()
+    s = o3.Setup3(n, n, n, 0.8)
+    m, _ = o3.link_mask(s)
+    B = o3.step(s, m, A)
+    del A
+    _, u_ref = o3.macros(s, m, B)
+    fl = m != o3.SOLID
+    assert rel_l2(f, B, fl) <= 1e-6
+    assert rel_l2(v, u_ref, fl) <= 1e-5
