@@ -669,6 +669,24 @@ def d3q19_rows(peak: float, stream, n: int = 256):
     return rows
 
 
+def d3q19_large(peak: float, stream, n: int = 1024, steps: int = 20):
+    """The D3Q19 FP32 step on a 1024^3 box (1.07e9 nodes, 163 GB of
+    lattices, 64-bit slot offsets) from rest: the working set the GPU's
+    memory allows, timed like the other rows."""
+    import torch
+    from paper_2108_13241_gb300 import lbm
+    sim = lbm.LBM3(n, n, n, 0.8, precision="f32")
+    sim.init_equilibrium(None, None)
+    t = time_steps(sim, steps, 5, stream)
+    gb = sim.workspace.numel() / 1e9
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    g = n ** 3 * steps / t / 1e9
+    return {"GLUPS": round(g, 3), "workspace_GB": round(gb, 1), "GBps_algorithmic": round(g * 152, 1),
+            "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
+
+
 def porosity_sweep(n: int = 4096, steps: int = 300, names=None, phis=None):
     """Sparse computational efficiency eta_P (Eq. 9) over porosity, Sec. 4.2.2's
     sweep: random discs r in [8, 256] (phi 0.1 .. 0.9), the regular 8 x 8 disc
@@ -905,7 +923,8 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         n = 256 if args.n == 4096 else args.n
-        res = {"sweep": "d3q19", "n": n, "results": d3q19_rows(peaks()[0], torch.cuda.current_stream(), n)}
+        res = {"sweep": "d3q19", "n": n, "results": d3q19_rows(peaks()[0], torch.cuda.current_stream(), n),
+               "rest_1024": d3q19_large(peaks()[0], torch.cuda.current_stream())}
         print(json.dumps(res), flush=True)
         return 0
     if args.sweep or args.porosity_sweep or args.channels or args.adjoint:

@@ -359,7 +359,7 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  *  sticky). */
 typedef struct lbm3_ctx lbm3_ctx;
 typedef struct {
-    int nx, ny, nz;              /* ny, nz <= 65535; 19*nx*ny*nz < 2^32 */
+    int nx, ny, nz;              /* ny, nz <= 65535; nx*ny*nz < 2^32 (1024^3 FP32 two-lattice: 163 GB) */
     const uint8_t *solid;        /* host [nz][ny][nx], 1 = solid; NULL = all fluid; read at create */
     double tau;                  /* > 0.5 (omega = 1/tau, Eq. 5) */
     double fx, fy, fz;           /* uniform body-force density (Guo) */

@@ -45,7 +45,8 @@ template <class T> __host__ __device__ constexpr T w3(int i) {
 struct Geo3 {
     int nx, ny, nz;
     int px, py, pz;        // periodic axes
-    unsigned N;            // nodes (19 N < 2^32, checked at create)
+    unsigned long long N;  // nodes (node indices are 32-bit: N < 2^32, checked at create;
+                           // slot offsets i N + n are 64-bit, so 19 N may exceed 2^32)
     const uint32_t *mask;  // [nz][ny][nx]; NULL: every node fluid, all axes periodic
 };
 struct Phys3 {
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(BLOCK3) k3_convert(const Geo3 g, const T *in, 
     const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
 #pragma unroll
     for (int i = 0; i < Q3; ++i) {
-        const unsigned k = (unsigned)i * g.N + n;
+        const unsigned long long k = (unsigned long long)i * g.N + n;
         out[k] = to_canonical ? in[k] + w3<T>(i) : in[k] - w3<T>(i);
     }
 }
@@ -271,7 +272,7 @@ const char *check3(const lbm3_params *p) {
     if (!p) return "params is NULL";
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "nx, ny, nz must be >= 1";
     if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
-    if ((double)Q3 * p->nx * p->ny * p->nz >= 4294967296.0) return "19*nx*ny*nz must be < 2^32";
+    if ((double)p->nx * p->ny * p->nz >= 4294967296.0) return "nx*ny*nz must be < 2^32";
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be > 0.5";
     if (!std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->fz)) return "force must be finite";
     if (p->precision != LBM_F64 && p->precision != LBM_F32) return "precision must be LBM_F64 or LBM_F32";
@@ -407,7 +408,7 @@ lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lb
     g.px = p->periodic_x != 0;
     g.py = p->periodic_y != 0;
     g.pz = p->periodic_z != 0;
-    g.N = (unsigned)((size_t)p->nx * p->ny * p->nz);
+    g.N = (unsigned long long)p->nx * p->ny * p->nz;
     g.mask = any ? reinterpret_cast<const uint32_t *>(ws + pl.offm) : nullptr;
     Phys3 &ph = c->ph;
     ph.om = 1.0 / p->tau;

@@ -191,3 +191,30 @@ def test_benchmark_box_one_step_matches_oracle(L, o3):
     fl = m != o3.SOLID
     assert rel_l2(f, B, fl) <= 1e-6
     assert rel_l2(v, u_ref, fl) <= 1e-5
+
+
+def test_box_beyond_32_bit_slot_offsets_equals_its_tiled_period(L):
+    """640^3 nodes (19 x 640^3 > 2^32 values a lattice: 64-bit slot offsets,
+    40 GB of FP32 lattices): a 3-D Taylor-Green field of period 64 tiled ten
+    times along each axis evolves exactly like the 64^3 box it tiles -- every
+    node does the same arithmetic on the same neighbour values, so the two
+    agree bit for bit after 20 steps."""
+    p, reps, steps = 64, 10, 20
+    rho, u = inputs.taylor_green_3d(p, p, p, 0.05)
+    r_s = torch.as_tensor(rho, dtype=torch.float32, device="cuda")
+    u_s = torch.as_tensor(u, dtype=torch.float32, device="cuda")
+    small = L.LBM3(p, p, p, 0.8, precision="f32")
+    small.init_equilibrium(r_s, u_s)
+    small.step(steps)
+    _, v_small = small.macros()
+    small.close()
+    n = p * reps
+    big = L.LBM3(n, n, n, 0.8, precision="f32")
+    assert 19 * n ** 3 > 2 ** 32
+    big.init_equilibrium(r_s.repeat(reps, reps, reps), u_s.repeat(1, reps, reps, reps))
+    big.step(steps)
+    _, v_big = big.macros()
+    big.close()
+    del big
+    tiled = v_small.repeat(1, reps, reps, reps)
+    assert torch.equal(v_big, tiled)
