@@ -645,27 +645,36 @@ def extra_measurements(args):
     return out
 
 
-def d3q19_rows(peak: float, stream, n: int = 256):
+def d3q19_rows(peak: float, stream, n: int = 256, steps: int = 200):
     """The D3Q19 step (lbm3_*) on an n^3 periodic 3-D Taylor-Green box
-    (U 0.05, tau 0.8): GLUPS and the fraction of the 2 x 19 x s bytes per
-    node (152 B FP32, 304 B FP64) at the measured HBM peak."""
+    (U 0.05, tau 0.8), FP64, FP32 and FP16-shifted storage, `steps` timed
+    steps after 10 warm-up ones: GLUPS, the fraction of the 2 x 19 x s bytes
+    per node (304 / 152 / 76 B) at the measured HBM peak, and the relative L2
+    error of u against the FP64 run after the same steps."""
     import torch
     from paper_2108_13241_gb300 import inputs, lbm
     rho, u = inputs.taylor_green_3d(n, n, n, 0.05)
     rows = {}
-    for prec, k in (("f32", 200), ("f64", 50)):
+    u64 = None
+    for prec in ("f64", "f32", "f16s"):
         sim = lbm.LBM3(n, n, n, 0.8, precision=prec)
         sim.init_equilibrium(rho, u)
-        t = time_steps(sim, k, 10, stream)
+        t = time_steps(sim, steps, 10, stream)
         _, v = sim.macros()
-        finite = bool(torch.isfinite(v).all())
+        v = v.double()
         sim.close()
         del sim
         torch.cuda.empty_cache()
-        g = n ** 3 * k / t / 1e9
+        g = n ** 3 * steps / t / 1e9
         nb = 2 * 19 * BYTES_PER_VALUE[prec]
         rows[prec] = {"GLUPS": round(g, 3), "bytes_per_node": nb, "GBps_algorithmic": round(g * nb, 1),
-                      "frac_of_measured_hbm": round(g * nb / peak, 4), "steps": k, "finite": finite}
+                      "frac_of_measured_hbm": round(g * nb / peak, 4), "steps": steps,
+                      "finite": bool(torch.isfinite(v).all())}
+        if u64 is None:
+            u64 = v
+        else:
+            rows[prec]["rel_l2_u_vs_f64"] = float(torch.linalg.vector_norm(v - u64) / torch.linalg.vector_norm(u64))
+        del v
     return rows
 
 

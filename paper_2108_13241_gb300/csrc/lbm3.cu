@@ -13,12 +13,14 @@
 // regrouped per pair of opposite links into an even part and an odd part
 // (exact algebra, fewer operations).  The register footprint stays small
 // (19 values a thread), the concern the paper raises for three dimensions.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm.h"
@@ -69,6 +71,31 @@ template <> struct P3<float> {
     }
 };
 
+// Stored element R <-> compute type (C): FP64 and FP32 store f - w as is;
+// FP16s stores binary16 bits of (f - w) * 2^10 (exact power-of-two scale, as
+// in two dimensions) and computes in FP32.
+template <class R> struct Cod3;
+template <> struct Cod3<double> {
+    typedef double C;
+    static __device__ __forceinline__ double dec(double r) { return r; }
+    static __device__ __forceinline__ double enc(double c) { return c; }
+};
+template <> struct Cod3<float> {
+    typedef float C;
+    static __device__ __forceinline__ float dec(float r) { return r; }
+    static __device__ __forceinline__ float enc(float c) { return c; }
+};
+constexpr float H3_SCALE = 1024.0f;
+template <> struct Cod3<unsigned short> {
+    typedef float C;
+    static __device__ __forceinline__ float dec(unsigned short r) {
+        return __half2float(__ushort_as_half(r)) * (1.0f / H3_SCALE);
+    }
+    static __device__ __forceinline__ unsigned short enc(float c) {
+        return __half_as_ushort(__float2half_rn(c * H3_SCALE));
+    }
+};
+
 // The node a thread updates, and its neighbours' coordinates along each
 // axis (periodic: wrapped; wall: clamped -- those links bounce and their
 // address is never used).
@@ -96,13 +123,14 @@ struct Node3 {
 
 // The gather of Algorithm 1 for one node: f'_i = A_i(x - c_i), or the
 // node's own value of the opposite link where link i bounces (bit i - 1).
-template <class T, bool HM>
-__device__ __forceinline__ void gather3(const Geo3 &g, const Node3 &nd, const T *A, uint32_t m, T f[Q3]) {
-    f[0] = A[nd.n];
+template <class R, bool HM>
+__device__ __forceinline__ void gather3(const Geo3 &g, const Node3 &nd, const R *A, uint32_t m,
+                                        typename Cod3<R>::C f[Q3]) {
+    f[0] = Cod3<R>::dec(A[nd.n]);
 #pragma unroll
     for (int i = 1; i < Q3; ++i) {
-        if (HM && (m & (1u << (i - 1)))) f[i] = A[(unsigned)opp3(i) * g.N + nd.n];
-        else f[i] = A[(unsigned)i * g.N + nd.src(g, i)];
+        if (HM && (m & (1u << (i - 1)))) f[i] = Cod3<R>::dec(A[(unsigned)opp3(i) * g.N + nd.n]);
+        else f[i] = Cod3<R>::dec(A[(unsigned)i * g.N + nd.src(g, i)]);
     }
 }
 
@@ -186,10 +214,91 @@ __global__ void __launch_bounds__(BLOCK3) k3_step(const Geo3 g, const Phys3 ph, 
     for (int i = 0; i < Q3; ++i) B[(unsigned)i * g.N + nd.n] = f[i];
 }
 
+// ---- FP16s storage: two nodes (x0 even, x0 + 1) per thread, rounded
+// together stochastically by one packed conversion per link, as in two
+// dimensions.
+__device__ __forceinline__ unsigned f16x2_rs3(float lo, float hi, unsigned rbits) {
+    unsigned r;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(rbits));
+    return r;
+}
+// counter-based random bits: the MurmurHash3 32-bit finaliser of (even
+// node's index, step seed), then one linear congruential step per link
+__device__ __forceinline__ unsigned fmix32_3(unsigned h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+template <bool HM, bool HAS_F>
+__global__ void __launch_bounds__(BLOCK3) k3_step_h(const Geo3 g, const Phys3 ph, const unsigned short *__restrict__ A,
+                                                    unsigned short *__restrict__ B, unsigned step) {
+    const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x0 >= g.nx) return; // nx is even
+    const int y = (int)blockIdx.y, z = (int)blockIdx.z;
+    const Node3 a(g, x0, y, z), b(g, x0 + 1, y, z);
+    uint32_t m0 = 0u, m1 = 0u;
+    if (HM) {
+        const uint2 mm = *reinterpret_cast<const uint2 *>(g.mask + a.n);
+        m0 = mm.x;
+        m1 = mm.y;
+        if (m0 == SOLID3 && m1 == SOLID3) return; // never read: nothing to store
+    }
+    // gather in units of the stored scale: links along y and z (c_x = 0)
+    // pull both nodes' values with one aligned 4-byte load
+    float f[2][Q3];
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) {
+        const unsigned long long so = (unsigned long long)i * g.N;
+        if (c3(i, 0) == 0) {
+            const unsigned w = *reinterpret_cast<const unsigned *>(A + so + a.src(g, i));
+            f[0][i] = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
+            f[1][i] = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+        } else {
+            f[0][i] = __half2float(__ushort_as_half(A[so + a.src(g, i)]));
+            f[1][i] = __half2float(__ushort_as_half(A[so + b.src(g, i)]));
+        }
+    }
+    if (HM && (m0 | m1)) {
+        // half-way bounce-back: the own node's value of the opposite link
+#pragma unroll
+        for (int i = 1; i < Q3; ++i) {
+            const uint32_t bit = 1u << (i - 1);
+            if ((m0 | m1) & bit) {
+                const unsigned w = *reinterpret_cast<const unsigned *>(A + (unsigned long long)opp3(i) * g.N + a.n);
+                if (m0 & bit) f[0][i] = __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
+                if (m1 & bit) f[1][i] = __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+            }
+        }
+    }
+    float Fx = ph.fx_f, Fy = ph.fy_f, Fz = ph.fz_f;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        // plain units for the collision, back to the stored scale after
+#pragma unroll
+        for (int i = 0; i < Q3; ++i) f[k][i] *= 1.0f / H3_SCALE;
+        collide3<float, HAS_F>(f[k], ph.om_f, ph.kk_f, Fx, Fy, Fz);
+        const bool solid = HM && (k == 0 ? m0 : m1) == SOLID3;
+#pragma unroll
+        for (int i = 0; i < Q3; ++i) f[k][i] = solid ? 0.0f : f[k][i] * H3_SCALE;
+    }
+    unsigned h = fmix32_3(a.n ^ fmix32_3(step * 0x9E3779B9u + 0x632BE5ABu));
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) {
+        h = h * 1664525u + 1013904223u;
+        *reinterpret_cast<unsigned *>(B + (unsigned long long)i * g.N + a.n) = f16x2_rs3(f[0][i], f[1][i], h ^ (h >> 16));
+    }
+}
+
 // rho and u at the current time (the gather without the collision); 0 at
 // solid nodes.
-template <class T>
-__global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph, const T *A, T *rho, T *u) {
+template <class R>
+__global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph, const R *A,
+                                                    typename Cod3<R>::C *rho, typename Cod3<R>::C *u) {
+    typedef typename Cod3<R>::C T;
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= g.nx) return;
     const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
@@ -201,8 +310,8 @@ __global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph
         return;
     }
     T f[Q3];
-    if (g.mask) gather3<T, true>(g, nd, A, m, f);
-    else gather3<T, false>(g, nd, A, m, f);
+    if (g.mask) gather3<R, true>(g, nd, A, m, f);
+    else gather3<R, false>(g, nd, A, m, f);
     T Fx, Fy, Fz, drho, jx, jy, jz;
     P3<T>::F(ph, Fx, Fy, Fz);
     moments3<T>(f, Fx, Fy, Fz, drho, jx, jy, jz);
@@ -217,8 +326,10 @@ __global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph
 
 // A = f^eq(rho, u) - w at fluid nodes (rho = 1, u = 0 where NULL), 0 (that
 // is, w) at solid nodes.
-template <class T>
-__global__ void __launch_bounds__(BLOCK3) k3_init(const Geo3 g, const T *rho, const T *u, T *A) {
+template <class R>
+__global__ void __launch_bounds__(BLOCK3) k3_init(const Geo3 g, const typename Cod3<R>::C *rho,
+                                                  const typename Cod3<R>::C *u, R *A) {
+    typedef typename Cod3<R>::C T;
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= g.nx) return;
     const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
@@ -230,20 +341,33 @@ __global__ void __launch_bounds__(BLOCK3) k3_init(const Geo3 g, const T *rho, co
     for (int i = 0; i < Q3; ++i) {
         const T t = T(c3(i, 0)) * ux + T(c3(i, 1)) * uy + T(c3(i, 2)) * uz;
         const T d = w3<T>(i) * ((r - T(1)) + r * (T(3) * t + T(4.5) * t * t - usq));
-        A[(unsigned)i * g.N + n] = solid ? T(0) : d;
+        A[(unsigned)i * g.N + n] = Cod3<R>::enc(solid ? T(0) : d);
     }
 }
 
 // canonical f = stored + w (get), stored = f - w (set)
-template <class T>
-__global__ void __launch_bounds__(BLOCK3) k3_convert(const Geo3 g, const T *in, T *out, int to_canonical) {
+template <class R>
+__global__ void __launch_bounds__(BLOCK3) k3_get(const Geo3 g, const R *in, typename Cod3<R>::C *out) {
+    typedef typename Cod3<R>::C T;
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= g.nx) return;
     const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
 #pragma unroll
     for (int i = 0; i < Q3; ++i) {
         const unsigned long long k = (unsigned long long)i * g.N + n;
-        out[k] = to_canonical ? in[k] + w3<T>(i) : in[k] - w3<T>(i);
+        out[k] = Cod3<R>::dec(in[k]) + w3<T>(i);
+    }
+}
+template <class R>
+__global__ void __launch_bounds__(BLOCK3) k3_set(const Geo3 g, const typename Cod3<R>::C *in, R *out) {
+    typedef typename Cod3<R>::C T;
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= g.nx) return;
+    const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) {
+        const unsigned long long k = (unsigned long long)i * g.N + n;
+        out[k] = Cod3<R>::enc(in[k] - w3<T>(i));
     }
 }
 
@@ -275,7 +399,8 @@ const char *check3(const lbm3_params *p) {
     if ((double)p->nx * p->ny * p->nz >= 4294967296.0) return "nx*ny*nz must be < 2^32";
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return "tau must be > 0.5";
     if (!std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->fz)) return "force must be finite";
-    if (p->precision != LBM_F64 && p->precision != LBM_F32) return "precision must be LBM_F64 or LBM_F32";
+    if (p->precision != LBM_F64 && p->precision != LBM_F32 && p->precision != LBM_F16S) return "unknown precision";
+    if (p->precision == LBM_F16S && (p->nx % 2)) return "FP16s storage needs an even nx (node pairs)";
     return nullptr;
 }
 
@@ -324,7 +449,7 @@ struct Plan3 {
 Plan3 plan3(const lbm3_params &p, bool has_mask) {
     Plan3 pl;
     const size_t N = (size_t)p.nx * p.ny * p.nz;
-    const size_t es = p.precision == LBM_F64 ? 8 : 4;
+    const size_t es = p.precision == LBM_F64 ? 8 : (p.precision == LBM_F32 ? 4 : 2);
     pl.lat = Q3 * N * es;
     pl.off1 = al256(pl.lat);
     pl.offm = pl.off1 + al256(pl.lat);
@@ -358,6 +483,22 @@ dim3 grid3(const Geo3 &g) {
 }
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+cudaError_t step3h(lbm3_ctx *c) {
+    const unsigned short *A = static_cast<const unsigned short *>(c->lat[c->cur]);
+    unsigned short *B = static_cast<unsigned short *>(c->lat[1 - c->cur]);
+    const bool F = c->p.fx != 0.0 || c->p.fy != 0.0 || c->p.fz != 0.0;
+    const int pairs = c->g.nx / 2;
+    const dim3 gr((unsigned)((pairs + BLOCK3 - 1) / BLOCK3), (unsigned)c->g.ny, (unsigned)c->g.nz);
+    const unsigned t = (unsigned)c->steps;
+    if (c->g.mask) {
+        if (F) k3_step_h<true, true><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B, t);
+        else k3_step_h<true, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B, t);
+    } else {
+        if (F) k3_step_h<false, true><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B, t);
+        else k3_step_h<false, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B, t);
+    }
+    return cudaGetLastError();
+}
 template <class T> cudaError_t step3(lbm3_ctx *c) {
     const T *A = static_cast<const T *>(c->lat[c->cur]);
     T *B = static_cast<T *>(c->lat[1 - c->cur]);
@@ -371,6 +512,13 @@ template <class T> cudaError_t step3(lbm3_ctx *c) {
         else k3_step<T, false, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
     }
     return cudaGetLastError();
+}
+
+// Calls f with a null pointer of the context's stored element type.
+template <class F> cudaError_t by_storage3(const lbm3_ctx *c, F f) {
+    if (c->es == 8) return f(static_cast<double *>(nullptr));
+    if (c->es == 4) return f(static_cast<float *>(nullptr));
+    return f(static_cast<unsigned short *>(nullptr));
 }
 
 } // namespace
@@ -395,7 +543,7 @@ lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lb
     lbm3_ctx *c = new lbm3_ctx();
     c->p = *p;
     c->p.solid = nullptr; // read here only
-    c->es = p->precision == LBM_F64 ? 8 : 4;
+    c->es = p->precision == LBM_F64 ? 8 : (p->precision == LBM_F32 ? 4 : 2);
     c->stream = static_cast<cudaStream_t>(p->stream);
     c->nfluid = nf;
     char *ws = static_cast<char *>(d_workspace);
@@ -451,24 +599,23 @@ lbm_status lbm3_init_equilibrium(lbm3_ctx *ctx, const void *d_rho, const void *d
     if ((d_rho && !aligned16(d_rho)) || (d_u && !aligned16(d_u)))
         return fail3(ctx, LBM_ERR_INVALID, "fields must be 16-byte aligned");
     const dim3 gr = grid3(ctx->g);
-    if (ctx->es == 8)
-        k3_init<double><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const double *>(d_rho),
-                                                         static_cast<const double *>(d_u),
-                                                         static_cast<double *>(ctx->lat[0]));
-    else
-        k3_init<float><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const float *>(d_rho),
-                                                       static_cast<const float *>(d_u),
-                                                       static_cast<float *>(ctx->lat[0]));
+    const cudaError_t e = by_storage3(ctx, [&](auto tag) {
+        typedef std::remove_pointer_t<decltype(tag)> R;
+        typedef typename Cod3<R>::C C;
+        k3_init<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const C *>(d_rho), static_cast<const C *>(d_u),
+                                                   static_cast<R *>(ctx->lat[0]));
+        return cudaGetLastError();
+    });
     ctx->cur = 0;
     ctx->steps = 0;
-    return cuda3(ctx, cudaGetLastError(), "init launch");
+    return cuda3(ctx, e, "init launch");
 }
 
 lbm_status lbm3_step(lbm3_ctx *ctx, int n) {
     LBM3_CHECK(ctx);
     if (n < 0) return fail3(ctx, LBM_ERR_INVALID, "n < 0");
     for (int k = 0; k < n; ++k) {
-        const cudaError_t e = ctx->es == 8 ? step3<double>(ctx) : step3<float>(ctx);
+        const cudaError_t e = ctx->es == 8 ? step3<double>(ctx) : (ctx->es == 4 ? step3<float>(ctx) : step3h(ctx));
         if (e != cudaSuccess) return cuda3(ctx, e, "step launch");
         ctx->cur = 1 - ctx->cur;
         ++ctx->steps;
@@ -481,38 +628,43 @@ lbm_status lbm3_macros(lbm3_ctx *ctx, void *d_rho, void *d_u) {
     if ((d_rho && !aligned16(d_rho)) || (d_u && !aligned16(d_u)))
         return fail3(ctx, LBM_ERR_INVALID, "fields must be 16-byte aligned");
     const dim3 gr = grid3(ctx->g);
-    if (ctx->es == 8)
-        k3_macros<double><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->ph,
-                                                           static_cast<const double *>(ctx->lat[ctx->cur]),
-                                                           static_cast<double *>(d_rho), static_cast<double *>(d_u));
-    else
-        k3_macros<float><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->ph,
-                                                         static_cast<const float *>(ctx->lat[ctx->cur]),
-                                                         static_cast<float *>(d_rho), static_cast<float *>(d_u));
-    return cuda3(ctx, cudaGetLastError(), "macros launch");
-}
-
-static lbm_status convert3(lbm3_ctx *ctx, const void *in, void *out, int to_canonical) {
-    const dim3 gr = grid3(ctx->g);
-    if (ctx->es == 8)
-        k3_convert<double><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const double *>(in),
-                                                            static_cast<double *>(out), to_canonical);
-    else
-        k3_convert<float><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const float *>(in),
-                                                          static_cast<float *>(out), to_canonical);
-    return cuda3(ctx, cudaGetLastError(), "convert launch");
+    return cuda3(ctx, by_storage3(ctx, [&](auto tag) {
+                     typedef std::remove_pointer_t<decltype(tag)> R;
+                     typedef typename Cod3<R>::C C;
+                     k3_macros<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->ph,
+                                                                  static_cast<const R *>(ctx->lat[ctx->cur]),
+                                                                  static_cast<C *>(d_rho), static_cast<C *>(d_u));
+                     return cudaGetLastError();
+                 }),
+                 "macros launch");
 }
 
 lbm_status lbm3_get_f(lbm3_ctx *ctx, void *d_f) {
     LBM3_CHECK(ctx);
     if (!d_f || !aligned16(d_f)) return fail3(ctx, LBM_ERR_INVALID, "f must be a 16-byte aligned pointer");
-    return convert3(ctx, ctx->lat[ctx->cur], d_f, 1);
+    const dim3 gr = grid3(ctx->g);
+    return cuda3(ctx, by_storage3(ctx, [&](auto tag) {
+                     typedef std::remove_pointer_t<decltype(tag)> R;
+                     typedef typename Cod3<R>::C C;
+                     k3_get<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const R *>(ctx->lat[ctx->cur]),
+                                                               static_cast<C *>(d_f));
+                     return cudaGetLastError();
+                 }),
+                 "get launch");
 }
 
 lbm_status lbm3_set_f(lbm3_ctx *ctx, const void *d_f) {
     LBM3_CHECK(ctx);
     if (!d_f || !aligned16(d_f)) return fail3(ctx, LBM_ERR_INVALID, "f must be a 16-byte aligned pointer");
-    return convert3(ctx, d_f, ctx->lat[ctx->cur], 0);
+    const dim3 gr = grid3(ctx->g);
+    return cuda3(ctx, by_storage3(ctx, [&](auto tag) {
+                     typedef std::remove_pointer_t<decltype(tag)> R;
+                     typedef typename Cod3<R>::C C;
+                     k3_set<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const C *>(d_f),
+                                                               static_cast<R *>(ctx->lat[ctx->cur]));
+                     return cudaGetLastError();
+                 }),
+                 "set launch");
 }
 
 long long lbm3_fluid_nodes(const lbm3_ctx *ctx) { return ctx ? ctx->nfluid : -1; }
