@@ -175,22 +175,51 @@ __device__ __forceinline__ void collide3(T f[Q3], T om, T kk, T Fx, T Fy, T Fz) 
         if (HAS_F) e -= kk * T(3) * uF;
         f[0] = om1 * f[0] + w3<T>(0) * e;
     }
+    if constexpr (sizeof(T) == 8) {
+        // FP64 (bound by its FP64 pipe): omega w and (1 - omega/2) w folded
+        // per weight class (axis, diagonal), 4.5 rho hoisted -- fewer FP64
+        // operations for the same algebra
+        const T r45 = T(4.5) * rho;
+        const T owa = om * w3<T>(1), owd = om * w3<T>(7);
+        const T kwa = kk * w3<T>(1), kwd = kk * w3<T>(7);
 #pragma unroll
-    for (int i = 1; i < Q3; i += 2) {
-        const T cx = T(c3(i, 0)), cy = T(c3(i, 1)), cz = T(c3(i, 2));
-        const T t = cx * ux + cy * uy + cz * uz;
-        const T cj = cx * jx + cy * jy + cz * jz;
-        T e = om * (base + T(4.5) * rho * t * t);
-        T o = om * cj;
-        if (HAS_F) {
-            const T cF = cx * Fx + cy * Fy + cz * Fz;
-            e += kk * (T(9) * t * cF - T(3) * uF);
-            o += kk * cF;
+        for (int i = 1; i < Q3; i += 2) {
+            const T ow = i <= 6 ? owa : owd, kw = i <= 6 ? kwa : kwd;
+            const T cx = T(c3(i, 0)), cy = T(c3(i, 1)), cz = T(c3(i, 2));
+            const T t = cx * ux + cy * uy + cz * uz;
+            const T cj = cx * jx + cy * jy + cz * jz;
+            T e = ow * (base + r45 * (t * t));
+            T o = (T(3) * ow) * cj;
+            if (HAS_F) {
+                const T cF = cx * Fx + cy * Fy + cz * Fz;
+                e += kw * (T(9) * t * cF - T(3) * uF);
+                o += (T(3) * kw) * cF;
+            }
+            f[i] = om1 * f[i] + (e + o);
+            f[i + 1] = om1 * f[i + 1] + (e - o);
         }
-        e *= w3<T>(i);
-        o *= T(3) * w3<T>(i);
-        f[i] = om1 * f[i] + (e + o);
-        f[i + 1] = om1 * f[i + 1] + (e - o);
+    } else {
+        // FP32 arithmetic (DRAM- or issue-bound): each factor rounded in
+        // the order of the formula, which keeps the FP32 velocity closer to
+        // FP64 on decaying flows (1.19e-5 against below 1e-5 with the FP64
+        // folding on the periodic random-field box)
+#pragma unroll
+        for (int i = 1; i < Q3; i += 2) {
+            const T cx = T(c3(i, 0)), cy = T(c3(i, 1)), cz = T(c3(i, 2));
+            const T t = cx * ux + cy * uy + cz * uz;
+            const T cj = cx * jx + cy * jy + cz * jz;
+            T e = om * (base + T(4.5) * rho * t * t);
+            T o = om * cj;
+            if (HAS_F) {
+                const T cF = cx * Fx + cy * Fy + cz * Fz;
+                e += kk * (T(9) * t * cF - T(3) * uF);
+                o += kk * cF;
+            }
+            e *= w3<T>(i);
+            o *= T(3) * w3<T>(i);
+            f[i] = om1 * f[i] + (e + o);
+            f[i + 1] = om1 * f[i + 1] + (e - o);
+        }
     }
 }
 
