@@ -158,11 +158,21 @@ __device__ __forceinline__ void moments3(const T f[Q3], T Fx, T Fy, T Fz, T &drh
 //   S_i = (1 - omega/2) w_i [3 (c_i . F) - 3 u.F + 9 t (c_i . F)],
 // taken per pair (i, opp(i)) as the even part E (the same for both) and the
 // odd part O = 3 w_i [omega (c_i . j) + (1 - omega/2) (c_i . F)] (+ for i,
-// - for opp(i)).
-template <class T, bool HAS_F>
+// - for opp(i)).  SC: f in units of 1/SC (FP16s computes on its stored
+// scale, SC = 2^10, so that neither its decode nor its encode multiplies);
+// the moments come back to plain units, the updates go out in f's units.
+template <class T, bool HAS_F, int SC = 1>
 __device__ __forceinline__ void collide3(T f[Q3], T om, T kk, T Fx, T Fy, T Fz) {
     T drho, jx, jy, jz;
-    moments3<T>(f, Fx, Fy, Fz, drho, jx, jy, jz);
+    if constexpr (SC == 1) {
+        moments3<T>(f, Fx, Fy, Fz, drho, jx, jy, jz);
+    } else {
+        moments3<T>(f, T(0), T(0), T(0), drho, jx, jy, jz);
+        drho *= T(1.0 / SC);
+        jx = jx * T(1.0 / SC) + T(0.5) * Fx;
+        jy = jy * T(1.0 / SC) + T(0.5) * Fy;
+        jz = jz * T(1.0 / SC) + T(0.5) * Fz;
+    }
     const T rho = T(1) + drho;
     const T inv = T(1) / rho;
     const T ux = jx * inv, uy = jy * inv, uz = jz * inv;
@@ -173,9 +183,10 @@ __device__ __forceinline__ void collide3(T f[Q3], T om, T kk, T Fx, T Fy, T Fz) 
     {
         T e = om * base;
         if (HAS_F) e -= kk * T(3) * uF;
-        f[0] = om1 * f[0] + w3<T>(0) * e;
+        f[0] = om1 * f[0] + (w3<T>(0) * T(SC)) * e;
     }
     if constexpr (sizeof(T) == 8) {
+        static_assert(SC == 1, "FP64 works in plain units");
         // FP64 (bound by its FP64 pipe): omega w and (1 - omega/2) w folded
         // per weight class (axis, diagonal), 4.5 rho hoisted -- fewer FP64
         // operations for the same algebra
@@ -215,8 +226,8 @@ __device__ __forceinline__ void collide3(T f[Q3], T om, T kk, T Fx, T Fy, T Fz) 
                 e += kk * (T(9) * t * cF - T(3) * uF);
                 o += kk * cF;
             }
-            e *= w3<T>(i);
-            o *= T(3) * w3<T>(i);
+            e *= w3<T>(i) * T(SC);
+            o *= T(3) * w3<T>(i) * T(SC);
             f[i] = om1 * f[i] + (e + o);
             f[i + 1] = om1 * f[i + 1] + (e - o);
         }
@@ -306,13 +317,11 @@ __global__ void __launch_bounds__(BLOCK3) k3_step_h(const Geo3 g, const Phys3 ph
     float Fx = ph.fx_f, Fy = ph.fy_f, Fz = ph.fz_f;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        // plain units for the collision, back to the stored scale after
-#pragma unroll
-        for (int i = 0; i < Q3; ++i) f[k][i] *= 1.0f / H3_SCALE;
-        collide3<float, HAS_F>(f[k], ph.om_f, ph.kk_f, Fx, Fy, Fz);
+        // the collision on the stored scale (values are (f - w) 2^10)
+        collide3<float, HAS_F, (int)H3_SCALE>(f[k], ph.om_f, ph.kk_f, Fx, Fy, Fz);
         const bool solid = HM && (k == 0 ? m0 : m1) == SOLID3;
 #pragma unroll
-        for (int i = 0; i < Q3; ++i) f[k][i] = solid ? 0.0f : f[k][i] * H3_SCALE;
+        for (int i = 0; i < Q3; ++i) f[k][i] = solid ? 0.0f : f[k][i];
     }
     unsigned h = fmix32_3(a.n ^ fmix32_3(step * 0x9E3779B9u + 0x632BE5ABu));
 #pragma unroll
