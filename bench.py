@@ -116,6 +116,39 @@ def fp64_alu_roofline(glups: float, sms: int):
             "GLUPS_ceiling": round(ceiling, 3), "frac": round(glups / ceiling, 4)}
 
 
+KERNEL3_SOURCE = os.path.join(ROOT, "paper_2108_13241_gb300", "csrc", "lbm3.cu")
+
+
+def kernel3_hash() -> str:
+    """Hash of the D3Q19 source (lbm3.cu) without comments and white space:
+    a profile figure of the 3-D step is used only while it matches."""
+    with open(KERNEL3_SOURCE) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    text = re.sub(r"\s+", "", text)
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
+def fp64_alu_roofline3(glups: float, sms: int):
+    """The FP64 D3Q19 step's FP64-pipe ceiling (FP64 instructions a node from
+    the committed capture of the same source), as fp64_alu_roofline."""
+    path = os.path.join(PROFILE_DIR, "step_d3q19_taylor_green_128.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    h = re.search(r"lbm3_source_sha256_16:\s*([0-9a-f]+)", text)
+    v = re.search(r"fp64_thread_instructions_per_node:\s*([0-9.eE+]+)", text)
+    if not h or not v or h.group(1) != kernel3_hash():
+        return None
+    per_node = float(v.group(1))
+    peak = FP64_PER_SM_CYCLE * sms * SM_MAX_HZ
+    ceiling = peak / per_node / 1e9
+    return {"bound": "alu", "fp64_inst_per_node": per_node, "peak_fp64_inst_per_s": peak,
+            "GLUPS_ceiling": round(ceiling, 3), "frac": round(glups / ceiling, 4)}
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
 
@@ -670,21 +703,36 @@ def d3q19_rows(peak: float, stream, n: int = 256, steps: int = 200):
         rows[prec] = {"GLUPS": round(g, 3), "bytes_per_node": nb, "GBps_algorithmic": round(g * nb, 1),
                       "frac_of_measured_hbm": round(g * nb / peak, 4), "steps": steps,
                       "finite": bool(torch.isfinite(v).all())}
+        if prec == "f64":
+            alu = fp64_alu_roofline3(g, torch.cuda.get_device_properties(0).multi_processor_count)
+            if alu is not None:
+                rows[prec]["alu_roofline"] = alu
         if u64 is None:
             u64 = v
         else:
             rows[prec]["rel_l2_u_vs_f64"] = float(torch.linalg.vector_norm(v - u64) / torch.linalg.vector_norm(u64))
         del v
+    # the in-place AA pattern, FP32
+    sim = lbm.LBM3(n, n, n, 0.8, precision="f32", pattern="aa")
+    sim.init_equilibrium(rho, u)
+    t = time_steps(sim, steps, 10, stream)
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    g = n ** 3 * steps / t / 1e9
+    rows["f32_aa"] = {"GLUPS": round(g, 3), "bytes_per_node": 152, "GBps_algorithmic": round(g * 152, 1),
+                      "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
     return rows
 
 
-def d3q19_large(peak: float, stream, n: int = 1024, steps: int = 20):
-    """The D3Q19 FP32 step on a 1024^3 box (1.07e9 nodes, 163 GB of
-    lattices, 64-bit slot offsets) from rest: the working set the GPU's
-    memory allows, timed like the other rows."""
+def d3q19_large(peak: float, stream, n: int = 1024, steps: int = 20, pattern: str = "two_lattice"):
+    """The D3Q19 FP32 step on a large box from rest -- 1024^3 two-lattice
+    (1.07e9 nodes, 163 GB) or 1280^3 AA (2.1e9 nodes, one 159 GB lattice),
+    64-bit slot offsets: the working sets the GPU's memory allows, timed
+    like the other rows."""
     import torch
     from paper_2108_13241_gb300 import lbm
-    sim = lbm.LBM3(n, n, n, 0.8, precision="f32")
+    sim = lbm.LBM3(n, n, n, 0.8, precision="f32", pattern=pattern)
     sim.init_equilibrium(None, None)
     t = time_steps(sim, steps, 5, stream)
     gb = sim.workspace.numel() / 1e9
@@ -692,8 +740,8 @@ def d3q19_large(peak: float, stream, n: int = 1024, steps: int = 20):
     del sim
     torch.cuda.empty_cache()
     g = n ** 3 * steps / t / 1e9
-    return {"GLUPS": round(g, 3), "workspace_GB": round(gb, 1), "GBps_algorithmic": round(g * 152, 1),
-            "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
+    return {"GLUPS": round(g, 3), "pattern": pattern, "workspace_GB": round(gb, 1),
+            "GBps_algorithmic": round(g * 152, 1), "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
 
 
 def porosity_sweep(n: int = 4096, steps: int = 300, names=None, phis=None):
@@ -935,8 +983,9 @@ def main():
         n = 256 if args.n == 4096 else args.n
         res = {"sweep": "d3q19", "n": n, "results": d3q19_rows(peaks()[0], torch.cuda.current_stream(), n)}
         if args.n == 4096:
-            # the 1024^3 box (163 GB) only in the default form of this mode
+            # the large boxes (163 / 159 GB) only in the default form of this mode
             res["rest_1024"] = d3q19_large(peaks()[0], torch.cuda.current_stream())
+            res["rest_1280_aa"] = d3q19_large(peaks()[0], torch.cuda.current_stream(), n=1280, pattern="aa")
         print(json.dumps(res), flush=True)
         return 0
     if args.sweep or args.porosity_sweep or args.channels or args.adjoint:

@@ -342,8 +342,9 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * dimensions, the extension the paper names as future work (Sec. 5).  The
  * moments (Eq. 2 with the Guo F/2 shift), the BGK relaxation (Eq. 3-5) and
  * the equilibrium (Eq. 6, with the D3Q19 weights 1/3 rest, 1/18 axis, 1/36
- * diagonal) are the two-dimensional step's; dense storage, two lattices,
- * stationary half-way bounce-back walls and obstacles, uniform body force.
+ * diagonal) are the two-dimensional step's; dense storage, two lattices or
+ * the in-place AA pattern, stationary half-way bounce-back walls and
+ * obstacles, uniform body force, FP64 / FP32 / FP16-shifted storage.
  *  Lattice: i = 0 rest; 1 (+1,0,0), 2 (-1,0,0), 3 (0,+1,0), 4 (0,-1,0),
  *  5 (0,0,+1), 6 (0,0,-1); 7 (+1,+1,0), 8 (-1,-1,0), 9 (+1,-1,0),
  *  10 (-1,+1,0); 11 (+1,0,+1), 12 (-1,0,-1), 13 (+1,0,-1), 14 (-1,0,+1);
@@ -364,13 +365,15 @@ typedef struct {
     double tau;                  /* > 0.5 (omega = 1/tau, Eq. 5) */
     double fx, fy, fz;           /* uniform body-force density (Guo) */
     int periodic_x, periodic_y, periodic_z; /* 0: stationary half-way bounce-back walls on both faces */
-    lbm_precision precision;     /* LBM_F64 or LBM_F32 */
+    lbm_precision precision;     /* LBM_F64, LBM_F32, or LBM_F16S (nx even; two-lattice only) */
+    lbm_pattern pattern;         /* LBM_TWO_LATTICE, or LBM_AA (one lattice, in place) */
     void *stream;                /* cudaStream_t; NULL = legacy default stream */
 } lbm3_params;
 
-/* Workspace bytes for p: two lattices (19 values a node) and, when some link
- * bounces, a 32-bit link mask per node.  Pure host; LBM_ERR_INVALID for bad
- * parameters. */
+/* Workspace bytes for p: two lattices (one for LBM_AA; 19 values a node)
+ * and, when some link bounces, a 32-bit link mask per node.  Pure host;
+ * LBM_ERR_INVALID for bad parameters (lbm3_create: LBM_ERR_UNSUPPORTED for
+ * FP16s with the AA pattern). */
 lbm_status lbm3_workspace_bytes(const lbm3_params *p, size_t *bytes);
 /* Builds the link mask on the host (bit i-1: link i pulls from a solid node
  * or across a wall face), carves the lattices and the mask out of

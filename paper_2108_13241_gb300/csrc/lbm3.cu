@@ -134,6 +134,44 @@ __device__ __forceinline__ void gather3(const Geo3 &g, const Node3 &nd, const R 
     }
 }
 
+// How the lattice holds the state A_t: two-lattice (slot i at x holds
+// A_i(x)); AA after its gather/scatter step's partner, the local step
+// (swapped: slot opp(i) at x holds A_i(x)); AA after a gather/scatter step
+// (streamed: slot i at x holds the next step's pulled f'_i(x)).
+enum Phase3 { P3_PLAIN = 0, P3_SWAPPED = 1, P3_STREAMED = 2 };
+
+// The next step's f'_i at node nd in any phase (bounced links: the own
+// node's value of the opposite link).
+template <class R, bool HM>
+__device__ __forceinline__ void gather3p(const Geo3 &g, const Node3 &nd, const R *A, uint32_t m, int phase,
+                                         typename Cod3<R>::C f[Q3]) {
+    if (phase == P3_PLAIN) {
+        gather3<R, HM>(g, nd, A, m, f);
+        return;
+    }
+    f[0] = Cod3<R>::dec(A[nd.n]);
+#pragma unroll
+    for (int i = 1; i < Q3; ++i) {
+        unsigned long long k;
+        if (phase == P3_STREAMED) k = (unsigned long long)i * g.N + nd.n;
+        else if (HM && (m & (1u << (i - 1)))) k = (unsigned long long)i * g.N + nd.n;
+        else k = (unsigned long long)opp3(i) * g.N + nd.src(g, i);
+        f[i] = Cod3<R>::dec(A[k]);
+    }
+}
+
+// Canonical A_i(x) read from any phase (streamed: the value the last
+// gather/scatter step pushed to x + c_i, or kept in the own opposite slot
+// where that link bounces).
+template <class R>
+__device__ __forceinline__ typename Cod3<R>::C canon3(const Geo3 &g, const Node3 &nd, const R *A, uint32_t m,
+                                                      int phase, int i) {
+    if (phase == P3_PLAIN || i == 0) return Cod3<R>::dec(A[(unsigned long long)i * g.N + nd.n]);
+    if (phase == P3_SWAPPED) return Cod3<R>::dec(A[(unsigned long long)opp3(i) * g.N + nd.n]);
+    if (m & (1u << (opp3(i) - 1))) return Cod3<R>::dec(A[(unsigned long long)opp3(i) * g.N + nd.n]);
+    return Cod3<R>::dec(A[(unsigned long long)i * g.N + nd.src(g, opp3(i))]); // x - c_opp(i) = x + c_i
+}
+
 // Moments of the shifted f' (Eq. 2 with the Guo shift): drho = rho - 1,
 // j = rho u = sum c f' + F/2.
 template <class T>
@@ -254,6 +292,39 @@ __global__ void __launch_bounds__(BLOCK3) k3_step(const Geo3 g, const Phys3 ph, 
     for (int i = 0; i < Q3; ++i) B[(unsigned)i * g.N + nd.n] = f[i];
 }
 
+// The in-place AA pattern, one lattice.  PULLPUSH (from the swapped
+// phase): f'_i = slot opp(i) at x - c_i (bounced: own slot i), collision,
+// f''_i to slot i at x + c_i (or, where that node is solid or beyond a
+// wall, to the own slot opp(i)) -- the streamed phase.  Local (from the
+// streamed phase): f'_i = own slot i, collision, f''_i to own slot opp(i)
+// -- the swapped phase.  Every (slot, node) is read and written by one
+// thread only, reads before writes, so the update in place is race-free.
+template <class T, bool HM, bool HAS_F, bool PULLPUSH>
+__global__ void __launch_bounds__(BLOCK3) k3_step_aa(const Geo3 g, const Phys3 ph, T *A) {
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= g.nx) return;
+    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
+    uint32_t m = 0u;
+    if (HM) {
+        m = g.mask[nd.n];
+        if (m == SOLID3) return;
+    }
+    T f[Q3];
+    gather3p<T, HM>(g, nd, A, m, PULLPUSH ? P3_SWAPPED : P3_STREAMED, f);
+    T Fx, Fy, Fz;
+    P3<T>::F(ph, Fx, Fy, Fz);
+    collide3<T, HAS_F>(f, P3<T>::om(ph), P3<T>::kk(ph), Fx, Fy, Fz);
+    A[nd.n] = f[0];
+#pragma unroll
+    for (int i = 1; i < Q3; ++i) {
+        unsigned long long k;
+        if (!PULLPUSH) k = (unsigned long long)opp3(i) * g.N + nd.n;
+        else if (HM && (m & (1u << (opp3(i) - 1)))) k = (unsigned long long)opp3(i) * g.N + nd.n;
+        else k = (unsigned long long)i * g.N + nd.src(g, opp3(i));
+        A[k] = f[i];
+    }
+}
+
 // ---- FP16s storage: two nodes (x0 even, x0 + 1) per thread, rounded
 // together stochastically by one packed conversion per link, as in two
 // dimensions.
@@ -334,7 +405,7 @@ __global__ void __launch_bounds__(BLOCK3) k3_step_h(const Geo3 g, const Phys3 ph
 // rho and u at the current time (the gather without the collision); 0 at
 // solid nodes.
 template <class R>
-__global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph, const R *A,
+__global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph, int phase, const R *A,
                                                     typename Cod3<R>::C *rho, typename Cod3<R>::C *u) {
     typedef typename Cod3<R>::C T;
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -348,8 +419,8 @@ __global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph
         return;
     }
     T f[Q3];
-    if (g.mask) gather3<R, true>(g, nd, A, m, f);
-    else gather3<R, false>(g, nd, A, m, f);
+    if (g.mask) gather3p<R, true>(g, nd, A, m, phase, f);
+    else gather3p<R, false>(g, nd, A, m, phase, f);
     T Fx, Fy, Fz, drho, jx, jy, jz;
     P3<T>::F(ph, Fx, Fy, Fz);
     moments3<T>(f, Fx, Fy, Fz, drho, jx, jy, jz);
@@ -365,7 +436,7 @@ __global__ void __launch_bounds__(BLOCK3) k3_macros(const Geo3 g, const Phys3 ph
 // A = f^eq(rho, u) - w at fluid nodes (rho = 1, u = 0 where NULL), 0 (that
 // is, w) at solid nodes.
 template <class R>
-__global__ void __launch_bounds__(BLOCK3) k3_init(const Geo3 g, const typename Cod3<R>::C *rho,
+__global__ void __launch_bounds__(BLOCK3) k3_init(const Geo3 g, int phase, const typename Cod3<R>::C *rho,
                                                   const typename Cod3<R>::C *u, R *A) {
     typedef typename Cod3<R>::C T;
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -379,33 +450,35 @@ __global__ void __launch_bounds__(BLOCK3) k3_init(const Geo3 g, const typename C
     for (int i = 0; i < Q3; ++i) {
         const T t = T(c3(i, 0)) * ux + T(c3(i, 1)) * uy + T(c3(i, 2)) * uz;
         const T d = w3<T>(i) * ((r - T(1)) + r * (T(3) * t + T(4.5) * t * t - usq));
-        A[(unsigned)i * g.N + n] = Cod3<R>::enc(solid ? T(0) : d);
+        A[(unsigned long long)(phase == P3_SWAPPED ? opp3(i) : i) * g.N + n] = Cod3<R>::enc(solid ? T(0) : d);
     }
 }
 
-// canonical f = stored + w (get), stored = f - w (set)
+// canonical f = stored + w (get, any phase), stored = f - w (set, plain or
+// swapped phase); solid nodes read w_i
 template <class R>
-__global__ void __launch_bounds__(BLOCK3) k3_get(const Geo3 g, const R *in, typename Cod3<R>::C *out) {
+__global__ void __launch_bounds__(BLOCK3) k3_get(const Geo3 g, int phase, const R *in, typename Cod3<R>::C *out) {
     typedef typename Cod3<R>::C T;
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= g.nx) return;
-    const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
+    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
+    const uint32_t m = g.mask ? g.mask[nd.n] : 0u;
 #pragma unroll
     for (int i = 0; i < Q3; ++i) {
-        const unsigned long long k = (unsigned long long)i * g.N + n;
-        out[k] = Cod3<R>::dec(in[k]) + w3<T>(i);
+        const T v = m == SOLID3 ? T(0) : canon3<R>(g, nd, in, m, phase, i);
+        out[(unsigned long long)i * g.N + nd.n] = v + w3<T>(i);
     }
 }
 template <class R>
-__global__ void __launch_bounds__(BLOCK3) k3_set(const Geo3 g, const typename Cod3<R>::C *in, R *out) {
+__global__ void __launch_bounds__(BLOCK3) k3_set(const Geo3 g, int phase, const typename Cod3<R>::C *in, R *out) {
     typedef typename Cod3<R>::C T;
     const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= g.nx) return;
     const unsigned n = (((unsigned)blockIdx.z * (unsigned)g.ny + blockIdx.y) * (unsigned)g.nx) + (unsigned)x;
 #pragma unroll
     for (int i = 0; i < Q3; ++i) {
-        const unsigned long long k = (unsigned long long)i * g.N + n;
-        out[k] = Cod3<R>::enc(in[k] - w3<T>(i));
+        const int slot = phase == P3_SWAPPED ? opp3(i) : i;
+        out[(unsigned long long)slot * g.N + n] = Cod3<R>::enc(in[(unsigned long long)i * g.N + n] - w3<T>(i));
     }
 }
 
@@ -420,6 +493,7 @@ struct lbm3_ctx {
     size_t es = 0;   // bytes per stored value
     void *lat[2] = {nullptr, nullptr};
     int cur = 0;     // lattice holding A_t
+    int phase = 0;   // Phase3 of the lattice
     long long steps = 0, nfluid = 0;
     cudaStream_t stream = nullptr;
     lbm_status sticky = LBM_OK;
@@ -439,6 +513,7 @@ const char *check3(const lbm3_params *p) {
     if (!std::isfinite(p->fx) || !std::isfinite(p->fy) || !std::isfinite(p->fz)) return "force must be finite";
     if (p->precision != LBM_F64 && p->precision != LBM_F32 && p->precision != LBM_F16S) return "unknown precision";
     if (p->precision == LBM_F16S && (p->nx % 2)) return "FP16s storage needs an even nx (node pairs)";
+    if (p->pattern != LBM_TWO_LATTICE && p->pattern != LBM_AA) return "unknown pattern";
     return nullptr;
 }
 
@@ -489,7 +564,7 @@ Plan3 plan3(const lbm3_params &p, bool has_mask) {
     const size_t N = (size_t)p.nx * p.ny * p.nz;
     const size_t es = p.precision == LBM_F64 ? 8 : (p.precision == LBM_F32 ? 4 : 2);
     pl.lat = Q3 * N * es;
-    pl.off1 = al256(pl.lat);
+    pl.off1 = p.pattern == LBM_AA ? 0 : al256(pl.lat); // AA: one lattice
     pl.offm = pl.off1 + al256(pl.lat);
     pl.has_mask = has_mask;
     pl.total = pl.offm + (has_mask ? al256(N * 4) : 0);
@@ -537,6 +612,24 @@ cudaError_t step3h(lbm3_ctx *c) {
     }
     return cudaGetLastError();
 }
+template <class T> cudaError_t step3aa(lbm3_ctx *c) {
+    T *A = static_cast<T *>(c->lat[0]);
+    const bool F = c->p.fx != 0.0 || c->p.fy != 0.0 || c->p.fz != 0.0;
+    const bool pp = c->phase == P3_SWAPPED;
+    const dim3 gr = grid3(c->g);
+#define LBM3_AA(HM, HF)                                                                    \
+    (pp ? (k3_step_aa<T, HM, HF, true><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A), 0)    \
+        : (k3_step_aa<T, HM, HF, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A), 0))
+    if (c->g.mask) {
+        if (F) LBM3_AA(true, true);
+        else LBM3_AA(true, false);
+    } else {
+        if (F) LBM3_AA(false, true);
+        else LBM3_AA(false, false);
+    }
+#undef LBM3_AA
+    return cudaGetLastError();
+}
 template <class T> cudaError_t step3(lbm3_ctx *c) {
     const T *A = static_cast<const T *>(c->lat[c->cur]);
     T *B = static_cast<T *>(c->lat[1 - c->cur]);
@@ -573,6 +666,7 @@ lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lb
     if (!out) return LBM_ERR_INVALID;
     *out = nullptr;
     if (check3(p) || !d_workspace || ((uintptr_t)d_workspace & 255u)) return LBM_ERR_INVALID;
+    if (p->pattern == LBM_AA && p->precision == LBM_F16S) return LBM_ERR_UNSUPPORTED;
     std::vector<uint32_t> mask;
     bool any = false;
     const long long nf = build_mask3(*p, mask, any);
@@ -587,6 +681,7 @@ lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lb
     char *ws = static_cast<char *>(d_workspace);
     c->lat[0] = ws;
     c->lat[1] = ws + pl.off1;
+    c->phase = p->pattern == LBM_AA ? P3_SWAPPED : P3_PLAIN;
     Geo3 &g = c->g;
     g.nx = p->nx;
     g.ny = p->ny;
@@ -637,11 +732,12 @@ lbm_status lbm3_init_equilibrium(lbm3_ctx *ctx, const void *d_rho, const void *d
     if ((d_rho && !aligned16(d_rho)) || (d_u && !aligned16(d_u)))
         return fail3(ctx, LBM_ERR_INVALID, "fields must be 16-byte aligned");
     const dim3 gr = grid3(ctx->g);
+    ctx->phase = ctx->p.pattern == LBM_AA ? P3_SWAPPED : P3_PLAIN;
     const cudaError_t e = by_storage3(ctx, [&](auto tag) {
         typedef std::remove_pointer_t<decltype(tag)> R;
         typedef typename Cod3<R>::C C;
-        k3_init<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const C *>(d_rho), static_cast<const C *>(d_u),
-                                                   static_cast<R *>(ctx->lat[0]));
+        k3_init<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->phase, static_cast<const C *>(d_rho),
+                                                   static_cast<const C *>(d_u), static_cast<R *>(ctx->lat[0]));
         return cudaGetLastError();
     });
     ctx->cur = 0;
@@ -653,9 +749,15 @@ lbm_status lbm3_step(lbm3_ctx *ctx, int n) {
     LBM3_CHECK(ctx);
     if (n < 0) return fail3(ctx, LBM_ERR_INVALID, "n < 0");
     for (int k = 0; k < n; ++k) {
-        const cudaError_t e = ctx->es == 8 ? step3<double>(ctx) : (ctx->es == 4 ? step3<float>(ctx) : step3h(ctx));
+        cudaError_t e;
+        if (ctx->p.pattern == LBM_AA) {
+            e = ctx->es == 8 ? step3aa<double>(ctx) : step3aa<float>(ctx);
+            ctx->phase = ctx->phase == P3_SWAPPED ? P3_STREAMED : P3_SWAPPED;
+        } else {
+            e = ctx->es == 8 ? step3<double>(ctx) : (ctx->es == 4 ? step3<float>(ctx) : step3h(ctx));
+            ctx->cur = 1 - ctx->cur;
+        }
         if (e != cudaSuccess) return cuda3(ctx, e, "step launch");
-        ctx->cur = 1 - ctx->cur;
         ++ctx->steps;
     }
     return LBM_OK;
@@ -669,7 +771,7 @@ lbm_status lbm3_macros(lbm3_ctx *ctx, void *d_rho, void *d_u) {
     return cuda3(ctx, by_storage3(ctx, [&](auto tag) {
                      typedef std::remove_pointer_t<decltype(tag)> R;
                      typedef typename Cod3<R>::C C;
-                     k3_macros<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->ph,
+                     k3_macros<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->ph, ctx->phase,
                                                                   static_cast<const R *>(ctx->lat[ctx->cur]),
                                                                   static_cast<C *>(d_rho), static_cast<C *>(d_u));
                      return cudaGetLastError();
@@ -684,7 +786,8 @@ lbm_status lbm3_get_f(lbm3_ctx *ctx, void *d_f) {
     return cuda3(ctx, by_storage3(ctx, [&](auto tag) {
                      typedef std::remove_pointer_t<decltype(tag)> R;
                      typedef typename Cod3<R>::C C;
-                     k3_get<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const R *>(ctx->lat[ctx->cur]),
+                     k3_get<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->phase,
+                                                               static_cast<const R *>(ctx->lat[ctx->cur]),
                                                                static_cast<C *>(d_f));
                      return cudaGetLastError();
                  }),
@@ -695,10 +798,11 @@ lbm_status lbm3_set_f(lbm3_ctx *ctx, const void *d_f) {
     LBM3_CHECK(ctx);
     if (!d_f || !aligned16(d_f)) return fail3(ctx, LBM_ERR_INVALID, "f must be a 16-byte aligned pointer");
     const dim3 gr = grid3(ctx->g);
+    ctx->phase = ctx->p.pattern == LBM_AA ? P3_SWAPPED : P3_PLAIN;
     return cuda3(ctx, by_storage3(ctx, [&](auto tag) {
                      typedef std::remove_pointer_t<decltype(tag)> R;
                      typedef typename Cod3<R>::C C;
-                     k3_set<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, static_cast<const C *>(d_f),
+                     k3_set<R><<<gr, BLOCK3, 0, ctx->stream>>>(ctx->g, ctx->phase, static_cast<const C *>(d_f),
                                                                static_cast<R *>(ctx->lat[ctx->cur]));
                      return cudaGetLastError();
                  }),

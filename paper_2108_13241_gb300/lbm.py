@@ -73,6 +73,7 @@ class lbm3_params(ctypes.Structure):
         ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("fz", ctypes.c_double),
         ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int), ("periodic_z", ctypes.c_int),
         ("precision", ctypes.c_int),
+        ("pattern", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -604,7 +605,7 @@ class LBM3:
     Canonical arrays: f [19, nz, ny, nx], u [3, nz, ny, nx], rho [nz, ny, nx]."""
 
     def __init__(self, nx: int, ny: int, nz: int, tau: float, solid=None, force=(0.0, 0.0, 0.0),
-                 periodic=(True, True, True), precision="f32", device="cuda"):
+                 periodic=(True, True, True), precision="f32", device="cuda", pattern="two_lattice"):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         p = lbm3_params()
         p.nx, p.ny, p.nz = self.nx, self.ny, self.nz
@@ -618,6 +619,7 @@ class LBM3:
         p.periodic_x, p.periodic_y, p.periodic_z = (int(bool(v)) for v in periodic)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         p.precision = prec
+        p.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
         p.stream = torch.cuda.current_stream().cuda_stream or None
         self.dtype = torch.float64 if prec == LBM_F64 else torch.float32
         self.device = torch.device(device)

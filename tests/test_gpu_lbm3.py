@@ -250,3 +250,45 @@ def test_fp16s_needs_even_nx(L):
     with pytest.raises(L.LBMError) as ei:
         L.LBM3(37, 8, 8, 0.8, precision="f16s")
     assert ei.value.status == L.LBM_ERR_INVALID
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+@pytest.mark.parametrize("name", ["porous_walls_force", "periodic_box", "ragged_all_walls"])
+def test_aa_pattern_equals_two_lattice(L, o3, name, steps, precision):
+    """The in-place AA pattern (one lattice, alternating gather/scatter and
+    local steps) gives the two-lattice step's state bit for bit after odd
+    and even step counts, and the same macros; it needs half the memory."""
+    s, solid, rho, u = setup(o3, name)
+    out = {}
+    for pattern in ("two_lattice", "aa"):
+        sim = L.LBM3(s.nx, s.ny, s.nz, s.tau, solid=solid, force=s.force, periodic=s.periodic,
+                     precision=precision, pattern=pattern)
+        sim.init_equilibrium(rho, u)
+        sim.step(steps)
+        r, v = sim.macros()
+        out[pattern] = (sim.get_f().cpu().numpy(), r.cpu().numpy(), v.cpu().numpy(), sim.workspace.numel())
+        sim.close()
+    m, _ = o3.link_mask(s, solid)
+    fl = m != o3.SOLID
+    f2, r2, u2, b2 = out["two_lattice"]
+    fa, ra, ua, ba = out["aa"]
+    assert np.array_equal(fa[:, fl], f2[:, fl])
+    assert np.array_equal(ra, r2) and np.array_equal(ua, u2)
+    assert ba < 0.6 * b2
+
+
+def test_aa_set_f_and_fp16s_refused(L, o3):
+    s, solid, rho, u = setup(o3, "porous_walls_force")
+    m, _ = o3.link_mask(s, solid)
+    A0 = o3.run(s, m, o3.init_equilibrium(s, m, rho, u), 3)
+    sim = L.LBM3(s.nx, s.ny, s.nz, s.tau, solid=solid, force=s.force, periodic=s.periodic,
+                 precision="f64", pattern="aa")
+    sim.set_f(A0)
+    sim.step(3)
+    B = o3.run(s, m, A0, 3)
+    assert rel_l2(sim.get_f().cpu().numpy(), B, m != o3.SOLID) <= 1e-13
+    sim.close()
+    with pytest.raises(L.LBMError) as ei:
+        L.LBM3(16, 8, 8, 0.8, precision="f16s", pattern="aa")
+    assert ei.value.status == L.LBM_ERR_UNSUPPORTED
