@@ -134,3 +134,59 @@ def test_geometry_with_open_sides_matches_oracle(lbm, orc, sides):
     mask, tid, nbr, nf = lbm.lbm_geometry(p)
     assert np.array_equal(mask, omask) and nf == onf
     assert np.array_equal(tid, otid) and np.array_equal(nbr, onbr)
+
+
+def _p3(lbm, nx=24, ny=10, nz=8, precision="f32", pattern="two_lattice", periodic=(1, 1, 1), solid=None, tau=0.8):
+    import ctypes
+    p = lbm.lbm3_params()
+    p.nx, p.ny, p.nz = nx, ny, nz
+    keep = None
+    if solid is not None:
+        keep = np.ascontiguousarray(solid, dtype=np.uint8)
+        p.solid = keep.ctypes.data_as(ctypes.c_void_p)
+    p.tau = tau
+    p.periodic_x, p.periodic_y, p.periodic_z = periodic
+    p.precision = lbm.PRECISIONS[precision]
+    p.pattern = lbm.PATTERNS[pattern]
+    return p, keep
+
+
+def _ws3(lbm, p):
+    import ctypes
+    n = ctypes.c_size_t(0)
+    st = lbm._load().lbm3_workspace_bytes(ctypes.byref(p), ctypes.byref(n))
+    return st, n.value
+
+
+def test_d3q19_workspace_counts_lattices_and_mask(lbm):
+    """Two lattices or one (AA) of 19 values a node, plus a 32-bit link mask
+    only when some link bounces (a wall axis or a solid node)."""
+    def al(b):
+        return (b + 255) // 256 * 256
+    nx, ny, nz = 24, 10, 8
+    N = nx * ny * nz
+    for prec, s in (("f64", 8), ("f32", 4), ("f16s", 2)):
+        for pat, nl in (("two_lattice", 2), ("aa", 1)):
+            if prec == "f16s" and pat == "aa":
+                continue
+            p, _ = _p3(lbm, nx, ny, nz, prec, pat)
+            st, b = _ws3(lbm, p)
+            assert st == lbm.LBM_OK and b == nl * al(19 * N * s)
+            p, _ = _p3(lbm, nx, ny, nz, prec, pat, periodic=(1, 0, 1))
+            st, b = _ws3(lbm, p)
+            assert st == lbm.LBM_OK and b == nl * al(19 * N * s) + al(4 * N)
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[3, 4, 5] = 1
+    p, keep = _p3(lbm, nx, ny, nz, "f32", solid=solid)
+    st, b = _ws3(lbm, p)
+    assert st == lbm.LBM_OK and b == 2 * al(19 * N * 4) + al(4 * N)
+
+
+@pytest.mark.parametrize("bad", [dict(ny=65536), dict(nz=0), dict(tau=0.5), dict(precision="f16s", nx=25),
+                                 dict(nx=2048, ny=2048, nz=1024)])
+def test_d3q19_invalid_parameters_rejected(lbm, bad):
+    kw = dict(nx=24, ny=10, nz=8, precision="f32", tau=0.8)
+    kw.update(bad)
+    p, _ = _p3(lbm, kw["nx"], kw["ny"], kw["nz"], kw["precision"], tau=kw["tau"])
+    st, _ = _ws3(lbm, p)
+    assert st == lbm.LBM_ERR_INVALID
