@@ -722,6 +722,22 @@ def d3q19_rows(peak: float, stream, n: int = 256, steps: int = 200):
     g = n ** 3 * steps / t / 1e9
     rows["f32_aa"] = {"GLUPS": round(g, 3), "bytes_per_node": 152, "GBps_algorithmic": round(g * 152, 1),
                       "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
+    # a porous medium of random overlapping spheres (r 8-16, porosity 0.5),
+    # periodic, force along x: the masked step with bounce-back, fluid-node
+    # GLUPS, two-lattice and AA, FP32
+    solid, phi = inputs.porous_spheres_3d(n, 0.5)
+    for pattern in ("two_lattice", "aa"):
+        sim = lbm.LBM3(n, n, n, 0.8, solid=solid, force=(1e-6, 0.0, 0.0), precision="f32", pattern=pattern)
+        nf = sim.fluid_nodes
+        sim.init_equilibrium(None, None)
+        t = time_steps(sim, steps, 10, stream)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        g = nf * steps / t / 1e9
+        rows["porous_spheres_phi%.2f/f32/%s" % (phi, pattern)] = {
+            "GLUPS": round(g, 3), "fluid_nodes": nf, "GBps_algorithmic": round(g * 152, 1),
+            "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
     return rows
 
 

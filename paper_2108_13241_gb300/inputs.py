@@ -293,3 +293,29 @@ def taylor_green_3d(nx: int, ny: int, nz: int, U: float):
     p = (U * U / 16.0) * (np.cos(2 * kx * x) + np.cos(2 * ky * y)) * (np.cos(2 * kz * z) + 2.0)
     rho = np.broadcast_to(1.0 + 3.0 * p, shape).copy()
     return rho, np.stack([ux, uy, uz])
+
+
+def porous_spheres_3d(n: int, porosity: float, rmin: float = 8.0, rmax: float = 16.0,
+                      seed: int = GEOMETRY_SEED):
+    """Three-dimensional porous medium on a periodic n^3 box: spheres with
+    uniform random centres and radii in [rmin, rmax], overlapping, added
+    until the solid fraction reaches 1 - porosity; integer-grid membership
+    |node - centre|^2 <= r^2 with periodic wrap.  Returns (solid uint8
+    [n, n, n] (z, y, x), achieved porosity)."""
+    rng = SplitMix64(seed)
+    solid = np.zeros((n, n, n), np.uint8)
+    target = (1.0 - porosity) * n ** 3
+    count = 0
+    while count < target:
+        c = [rng.uniform(0, n) for _ in range(3)]
+        r = rng.uniform(rmin, rmax)
+        lo = [int(math.floor(ci - r)) for ci in c]
+        hi = [int(math.ceil(ci + r)) + 1 for ci in c]
+        zz, yy, xx = np.meshgrid(np.arange(lo[2], hi[2]), np.arange(lo[1], hi[1]), np.arange(lo[0], hi[0]),
+                                 indexing="ij")
+        inside = (xx - c[0]) ** 2 + (yy - c[1]) ** 2 + (zz - c[2]) ** 2 <= r * r
+        idx = (zz[inside] % n, yy[inside] % n, xx[inside] % n)
+        before = int(solid[idx].sum())
+        solid[idx] = 1
+        count += int(solid[idx].sum()) - before
+    return solid, 1.0 - count / n ** 3

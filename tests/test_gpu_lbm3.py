@@ -292,3 +292,28 @@ def test_aa_set_f_and_fp16s_refused(L, o3):
     with pytest.raises(L.LBMError) as ei:
         L.LBM3(16, 8, 8, 0.8, precision="f16s", pattern="aa")
     assert ei.value.status == L.LBM_ERR_UNSUPPORTED
+
+
+def test_porous_spheres_crop_matches_oracle(L, o3):
+    """A 48^3 crop of the benchmark's 3-D porous medium (random spheres,
+    porosity 0.5), walls on the z faces, force along x: FP64 within 1e-12 of
+    the oracle on f, FP32 within 1e-5 on u, two-lattice and AA, 60 steps."""
+    solid_full, _ = inputs.porous_spheres_3d(256, 0.5)
+    solid = np.ascontiguousarray(solid_full[:48, :48, :48])
+    s = o3.Setup3(48, 48, 48, 0.8, periodic=(True, True, False), force=(1e-5, 0.0, 0.0))
+    m, _ = o3.link_mask(s, solid)
+    A = o3.run(s, m, o3.init_equilibrium(s, m), 60)
+    _, u_ref = o3.macros(s, m, A)
+    fl = m != o3.SOLID
+    for prec in ("f64", "f32"):
+        for pattern in ("two_lattice", "aa"):
+            sim = L.LBM3(48, 48, 48, 0.8, solid=solid, force=s.force, periodic=s.periodic, precision=prec,
+                         pattern=pattern)
+            sim.init_equilibrium(None, None)
+            sim.step(60)
+            f = sim.get_f().double().cpu().numpy()
+            _, v = sim.macros()
+            sim.close()
+            if prec == "f64":
+                assert rel_l2(f, A, fl) <= 1e-12, pattern
+            assert rel_l2(v.double().cpu().numpy(), u_ref, fl) <= 1e-5, (prec, pattern)
