@@ -120,10 +120,13 @@ KERNEL3_SOURCE = os.path.join(ROOT, "paper_2108_13241_gb300", "csrc", "lbm3.cu")
 
 
 def kernel3_hash() -> str:
-    """Hash of the D3Q19 source (lbm3.cu) without comments and white space:
-    a profile figure of the 3-D step is used only while it matches."""
+    """Hash of the D3Q19 device code (lbm3.cu before its C-ABI section: the
+    kernels, not the host code that builds tables and picks them) without
+    comments and white space: a profile figure of the 3-D step is used only
+    while it matches."""
     with open(KERNEL3_SOURCE) as fh:
         text = fh.read()
+    text = text[:text.index("// " + "-" * 61 + " C ABI")]
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     text = re.sub(r"//[^\n]*", "", text)
     text = re.sub(r"\s+", "", text)
@@ -724,20 +727,25 @@ def d3q19_rows(peak: float, stream, n: int = 256, steps: int = 200):
                       "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
     # a porous medium of random overlapping spheres (r 8-16, porosity 0.5),
     # periodic, force along x: the masked step with bounce-back, fluid-node
-    # GLUPS, two-lattice and AA, FP32
+    # GLUPS, two-lattice and AA, FP32; the library's own choice (AA: the node
+    # list; two lattices: the dense grid) and, for comparison, the other one
     solid, phi = inputs.porous_spheres_3d(n, 0.5)
     for pattern in ("two_lattice", "aa"):
-        sim = lbm.LBM3(n, n, n, 0.8, solid=solid, force=(1e-6, 0.0, 0.0), precision="f32", pattern=pattern)
-        nf = sim.fluid_nodes
-        sim.init_equilibrium(None, None)
-        t = time_steps(sim, steps, 10, stream)
-        sim.close()
-        del sim
-        torch.cuda.empty_cache()
-        g = nf * steps / t / 1e9
-        rows["porous_spheres_phi%.2f/f32/%s" % (phi, pattern)] = {
-            "GLUPS": round(g, 3), "fluid_nodes": nf, "GBps_algorithmic": round(g * 152, 1),
-            "frac_of_measured_hbm": round(g * 152 / peak, 4), "steps": steps}
+        for mode in ("auto", "never" if pattern == "aa" else "always"):
+            sim = lbm.LBM3(n, n, n, 0.8, solid=solid, force=(1e-6, 0.0, 0.0), precision="f32", pattern=pattern,
+                           node_list=mode)
+            nf, nl = sim.fluid_nodes, sim.list_nodes
+            sim.init_equilibrium(None, None)
+            t = time_steps(sim, steps, 10, stream)
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
+            g = nf * steps / t / 1e9
+            key = "porous_spheres_phi%.2f/f32/%s" % (phi, pattern) + {"auto": "", "never": "/dense_grid",
+                                                                        "always": "/node_list"}[mode]
+            rows[key] = {"GLUPS": round(g, 3), "fluid_nodes": nf, "listed_nodes": nl,
+                         "GBps_algorithmic": round(g * 152, 1), "frac_of_measured_hbm": round(g * 152 / peak, 4),
+                         "steps": steps}
     return rows
 
 

@@ -368,10 +368,22 @@ typedef struct {
     lbm_precision precision;     /* LBM_F64, LBM_F32, or LBM_F16S (nx even; two-lattice only) */
     lbm_pattern pattern;         /* LBM_TWO_LATTICE, or LBM_AA (one lattice, in place) */
     void *stream;                /* cudaStream_t; NULL = legacy default stream */
+    int node_list;               /* FP64 / FP32 with a link mask: 0 = a node list with the
+                                    AA pattern when it holds at most 90% of the nodes (two
+                                    lattices: the dense grid, measured faster), 1 = never
+                                    (the dense grid), 2 = always; ignored for FP16s (below) */
 } lbm3_params;
 
-/* Workspace bytes for p: two lattices (one for LBM_AA; 19 values a node)
- * and, when some link bounces, a 32-bit link mask per node.  Pure host;
+/* The node list (sparse geometries; the porous-media counterpart of the
+ * two-dimensional tiles of Sec. 4.2.2): the step runs one thread per listed
+ * node instead of one per grid node, so no lane idles on a solid node.  It
+ * lists, ascending, every fluid node and, with two lattices, every solid
+ * node sharing a 32-byte sector of the slot planes with a fluid node (it
+ * stores zeros, so sectors are written whole); 8 bytes an entry in the
+ * workspace (the node index and its link mask, read by one load).  Results are bit-identical to the dense grid's. */
+
+/* Workspace bytes for p: two lattices (one for LBM_AA; 19 values a node),
+ * when some link bounces a 32-bit link mask per node, and the node list.  Pure host;
  * LBM_ERR_INVALID for bad parameters (lbm3_create: LBM_ERR_UNSUPPORTED for
  * FP16s with the AA pattern). */
 lbm_status lbm3_workspace_bytes(const lbm3_params *p, size_t *bytes);
@@ -394,6 +406,9 @@ lbm_status lbm3_macros(lbm3_ctx *ctx, void *d_rho, void *d_u);
 lbm_status lbm3_get_f(lbm3_ctx *ctx, void *d_f);
 lbm_status lbm3_set_f(lbm3_ctx *ctx, const void *d_f);
 long long lbm3_fluid_nodes(const lbm3_ctx *ctx);
+/* Entries of the node list the step runs over; 0 when it runs over the
+ * dense grid; -1 for a NULL ctx. */
+long long lbm3_list_nodes(const lbm3_ctx *ctx);
 long long lbm3_step_count(const lbm3_ctx *ctx);
 const char *lbm3_last_error(const lbm3_ctx *ctx);
 

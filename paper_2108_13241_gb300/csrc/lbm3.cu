@@ -50,7 +50,26 @@ struct Geo3 {
     unsigned long long N;  // nodes (node indices are 32-bit: N < 2^32, checked at create;
                            // slot offsets i N + n are 64-bit, so 19 N may exceed 2^32)
     const uint32_t *mask;  // [nz][ny][nx]; NULL: every node fluid, all axes periodic
+    const uint2 *list;     // node list of the listed step (node index, link mask; ascending
+                           // index); NULL: the dense grid runs
+    unsigned nlist;        // entries of list
+    unsigned mx, my;       // floor((2^32 - 1) / nx), floor((2^32 - 1) / ny): node index -> x, y, z
 };
+
+// q = n / d and r = n mod d for a divisor fixed for the run: the high word
+// of n * floor((2^32 - 1) / d) lies between n / d - 2 and n / d (n < 2^32),
+// so at most two corrections follow.
+__device__ __forceinline__ unsigned divq3(unsigned n, unsigned d, unsigned magic, unsigned &r) {
+    unsigned q = __umulhi(n, magic);
+    r = n - q * d;
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        if (r >= d) {
+            ++q;
+            r -= d;
+        }
+    return q;
+}
 struct Phys3 {
     double om, kk, fx, fy, fz; // omega = 1/tau, 1 - omega/2, force
     float om_f, kk_f, fx_f, fy_f, fz_f;
@@ -103,11 +122,19 @@ struct Node3 {
     int x, y, z;
     unsigned n;
     int xs[3], ys[3], zs[3]; // coordinate - 1, itself, + 1
-    __device__ __forceinline__ Node3(const Geo3 &g, int x_, int y_, int z_) : x(x_), y(y_), z(z_) {
-        n = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx + (unsigned)x;
+    __device__ __forceinline__ Node3(const Geo3 &g, int x_, int y_, int z_)
+        : Node3(g, x_, y_, z_, ((unsigned)z_ * (unsigned)g.ny + (unsigned)y_) * (unsigned)g.nx + (unsigned)x_) {}
+    __device__ __forceinline__ Node3(const Geo3 &g, int x_, int y_, int z_, unsigned n_) : x(x_), y(y_), z(z_), n(n_) {
         nb(x, g.nx, g.px, xs);
         nb(y, g.ny, g.py, ys);
         nb(z, g.nz, g.pz, zs);
+    }
+    // the node of index n_ (an entry of the node list)
+    static __device__ __forceinline__ Node3 at(const Geo3 &g, unsigned n_) {
+        unsigned x_, y_;
+        const unsigned row = divq3(n_, (unsigned)g.nx, g.mx, x_);
+        const unsigned z_ = divq3(row, (unsigned)g.ny, g.my, y_);
+        return Node3(g, (int)x_, (int)y_, (int)z_, n_);
     }
     static __device__ __forceinline__ void nb(int c, int n, int per, int o[3]) {
         o[0] = c > 0 ? c - 1 : (per ? n - 1 : 0);
@@ -272,17 +299,23 @@ __device__ __forceinline__ void collide3(T f[Q3], T om, T kk, T Fx, T Fy, T Fz) 
     }
 }
 
+// Whether a solid node shares its 32-byte DRAM sector with a fluid node of
+// its warp (lanes in aligned groups of 32 / bytes-per-lane): such a node
+// writes zeros -- what every solid node holds, and never read -- so that the
+// sector is stored whole and the memory does not first read the old sector
+// to merge a partial write (the two-lattice step writes a lattice it has not
+// read).  `fluid` is the warp's ballot of lanes holding fluid.
+template <int LANE_BYTES> __device__ __forceinline__ bool sector_has_fluid(unsigned fluid) {
+    constexpr int G = 32 / LANE_BYTES;
+    const int lane = (int)(threadIdx.x & 31u);
+    return ((fluid >> (lane & ~(G - 1))) & ((1u << G) - 1u)) != 0u;
+}
+
+// One node's two-lattice update (Algorithm 1): the gather, the collision and
+// the aligned stores of its 19 values to B.
 template <class T, bool HM, bool HAS_F>
-__global__ void __launch_bounds__(BLOCK3) k3_step(const Geo3 g, const Phys3 ph, const T *__restrict__ A,
-                                                  T *__restrict__ B) {
-    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (x >= g.nx) return;
-    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
-    uint32_t m = 0u;
-    if (HM) {
-        m = g.mask[nd.n];
-        if (m == SOLID3) return; // never read: nothing to store
-    }
+__device__ __forceinline__ void step_node3(const Geo3 &g, const Phys3 &ph, const T *__restrict__ A,
+                                           T *__restrict__ B, const Node3 &nd, uint32_t m) {
     T f[Q3];
     gather3<T, HM>(g, nd, A, m, f);
     T Fx, Fy, Fz;
@@ -290,6 +323,51 @@ __global__ void __launch_bounds__(BLOCK3) k3_step(const Geo3 g, const Phys3 ph, 
     collide3<T, HAS_F>(f, P3<T>::om(ph), P3<T>::kk(ph), Fx, Fy, Fz);
 #pragma unroll
     for (int i = 0; i < Q3; ++i) B[(unsigned)i * g.N + nd.n] = f[i];
+}
+
+template <class T, bool HM, bool HAS_F>
+__global__ void __launch_bounds__(BLOCK3) k3_step(const Geo3 g, const Phys3 ph, const T *__restrict__ A,
+                                                  T *__restrict__ B) {
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (!HM && x >= g.nx) return;
+    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
+    uint32_t m = 0u;
+    if (HM) {
+        // every lane of the warp takes part in the ballot (blocks are whole
+        // warps); lanes beyond the row count as solid and touch no memory
+        const bool in = x < g.nx;
+        m = in ? g.mask[nd.n] : SOLID3;
+        const unsigned fluid = __ballot_sync(0xFFFFFFFFu, m != SOLID3);
+        if (!in) return;
+        if (m == SOLID3) {
+            if (sector_has_fluid<(int)sizeof(T)>(fluid)) {
+#pragma unroll
+                for (int i = 0; i < Q3; ++i) B[(unsigned)i * g.N + nd.n] = T(0);
+            }
+            return; // never read
+        }
+    }
+    step_node3<T, HM, HAS_F>(g, ph, A, B, nd, m);
+}
+
+// The listed two-lattice step: one thread per entry of the node list -- the
+// fluid nodes, and the solid nodes that share a DRAM sector with one (they
+// store zeros, as above) -- so no lane of a porous box idles on a solid
+// node; the entries' coordinates come from their index.
+template <class T, bool HAS_F>
+__global__ void __launch_bounds__(BLOCK3) k3_step_list(const Geo3 g, const Phys3 ph, const T *__restrict__ A,
+                                                       T *__restrict__ B) {
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.nlist) return;
+    const uint2 e = g.list[t]; // the node and its mask in one load: no dependent mask read
+    const unsigned n = e.x;
+    const uint32_t m = e.y;
+    if (m == SOLID3) {
+#pragma unroll
+        for (int i = 0; i < Q3; ++i) B[(unsigned long long)i * g.N + n] = T(0);
+        return;
+    }
+    step_node3<T, true, HAS_F>(g, ph, A, B, Node3::at(g, n), m);
 }
 
 // The in-place AA pattern, one lattice.  PULLPUSH (from the swapped
@@ -300,15 +378,7 @@ __global__ void __launch_bounds__(BLOCK3) k3_step(const Geo3 g, const Phys3 ph, 
 // -- the swapped phase.  Every (slot, node) is read and written by one
 // thread only, reads before writes, so the update in place is race-free.
 template <class T, bool HM, bool HAS_F, bool PULLPUSH>
-__global__ void __launch_bounds__(BLOCK3) k3_step_aa(const Geo3 g, const Phys3 ph, T *A) {
-    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (x >= g.nx) return;
-    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
-    uint32_t m = 0u;
-    if (HM) {
-        m = g.mask[nd.n];
-        if (m == SOLID3) return;
-    }
+__device__ __forceinline__ void step_node3_aa(const Geo3 &g, const Phys3 &ph, T *A, const Node3 &nd, uint32_t m) {
     T f[Q3];
     gather3p<T, HM>(g, nd, A, m, PULLPUSH ? P3_SWAPPED : P3_STREAMED, f);
     T Fx, Fy, Fz;
@@ -323,6 +393,34 @@ __global__ void __launch_bounds__(BLOCK3) k3_step_aa(const Geo3 g, const Phys3 p
         else k = (unsigned long long)i * g.N + nd.src(g, opp3(i));
         A[k] = f[i];
     }
+}
+
+template <class T, bool HM, bool HAS_F, bool PULLPUSH>
+__global__ void __launch_bounds__(BLOCK3, sizeof(T) == 4 ? 6 : 1) k3_step_aa(const Geo3 g, const Phys3 ph, T *A) {
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= g.nx) return;
+    const Node3 nd(g, x, (int)blockIdx.y, (int)blockIdx.z);
+    uint32_t m = 0u;
+    if (HM) {
+        m = g.mask[nd.n];
+        if (m == SOLID3) return;
+    }
+    step_node3_aa<T, HM, HAS_F, PULLPUSH>(g, ph, A, nd, m);
+}
+
+// The listed AA step: one thread per fluid node of the node list (the AA
+// pattern's list holds fluid nodes only; its in-place stores touch sectors
+// the same warp has just read).
+template <class T, bool HAS_F, bool PULLPUSH>
+__global__ void __launch_bounds__(BLOCK3, sizeof(T) == 4 ? 6 : 1) k3_step_aa_list(const Geo3 g, const Phys3 ph,
+                                                                                 T *A) {
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.nlist) return;
+    const uint2 e = g.list[t];
+    const unsigned n = e.x;
+    const uint32_t m = e.y;
+    if (m == SOLID3) return;
+    step_node3_aa<T, true, HAS_F, PULLPUSH>(g, ph, A, Node3::at(g, n), m);
 }
 
 // ---- FP16s storage: two nodes (x0 even, x0 + 1) per thread, rounded
@@ -348,15 +446,33 @@ template <bool HM, bool HAS_F>
 __global__ void __launch_bounds__(BLOCK3) k3_step_h(const Geo3 g, const Phys3 ph, const unsigned short *__restrict__ A,
                                                     unsigned short *__restrict__ B, unsigned step) {
     const int x0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (x0 >= g.nx) return; // nx is even
+    if (!HM && x0 >= g.nx) return; // nx is even
     const int y = (int)blockIdx.y, z = (int)blockIdx.z;
     const Node3 a(g, x0, y, z), b(g, x0 + 1, y, z);
     uint32_t m0 = 0u, m1 = 0u;
     if (HM) {
-        const uint2 mm = *reinterpret_cast<const uint2 *>(g.mask + a.n);
-        m0 = mm.x;
-        m1 = mm.y;
-        if (m0 == SOLID3 && m1 == SOLID3) return; // never read: nothing to store
+        // the whole warp votes (as in k3_step); lanes beyond the row count
+        // as solid and touch no memory
+        const bool in = x0 < g.nx;
+        if (in) {
+            const uint2 mm = *reinterpret_cast<const uint2 *>(g.mask + a.n);
+            m0 = mm.x;
+            m1 = mm.y;
+        } else {
+            m0 = m1 = SOLID3;
+        }
+        const unsigned fluid = __ballot_sync(0xFFFFFFFFu, m0 != SOLID3 || m1 != SOLID3);
+        if (!in) return;
+        if (m0 == SOLID3 && m1 == SOLID3) {
+            // never read; zeros where the sector holds fluid (whole-sector
+            // stores)
+            if (sector_has_fluid<4>(fluid)) {
+#pragma unroll
+                for (int i = 0; i < Q3; ++i)
+                    *reinterpret_cast<unsigned *>(B + (unsigned long long)i * g.N + a.n) = 0u;
+            }
+            return;
+        }
     }
     // gather in units of the stored scale: links along y and z (c_x = 0)
     // pull both nodes' values with one aligned 4-byte load
@@ -514,6 +630,7 @@ const char *check3(const lbm3_params *p) {
     if (p->precision != LBM_F64 && p->precision != LBM_F32 && p->precision != LBM_F16S) return "unknown precision";
     if (p->precision == LBM_F16S && (p->nx % 2)) return "FP16s storage needs an even nx (node pairs)";
     if (p->pattern != LBM_TWO_LATTICE && p->pattern != LBM_AA) return "unknown pattern";
+    if (p->node_list < 0 || p->node_list > 2) return "node_list must be 0, 1 or 2";
     return nullptr;
 }
 
@@ -555,11 +672,49 @@ long long build_mask3(const lbm3_params &p, std::vector<uint32_t> &m, bool &any)
     return nf;
 }
 
+// The node list of the listed step, ascending: every fluid node and, with
+// two lattices, every solid node that shares a 32-byte sector of the stored
+// slot planes with a fluid node (it stores zeros there, so the sector is
+// written whole).  Built for FP64 / FP32 storage when some link bounces,
+// and used when node_list is 2, or 0 with the AA pattern and at most 90% of
+// the nodes listed (with two lattices the dense grid measured faster: its
+// zero-storing solid lanes ride in warps that hold fluid anyway, while in
+// the list they take lanes of their own); otherwise empty and the dense
+// grid runs.  Returns the entries; with
+// `mask` (the link mask) and `out`, writes them as (node index, its mask).
+size_t node_list3(const lbm3_params &p, bool has_mask, const std::vector<uint32_t> *mask, std::vector<uint2> *out) {
+    if (out) out->clear();
+    if (!has_mask || p.precision == LBM_F16S || p.node_list == 1) return 0;
+    const size_t N = (size_t)p.nx * p.ny * p.nz;
+    const size_t G = p.precision == LBM_F64 ? 4 : 8; // nodes per 32-byte sector
+    const bool two = p.pattern == LBM_TWO_LATTICE;
+    auto fluid = [&](size_t k) { return !(p.solid && p.solid[k]); };
+    // calls fn on the listed nodes in ascending order
+    auto visit = [&](auto fn) {
+        for (size_t s0 = 0; s0 < N; s0 += G) {
+            const size_t s1 = s0 + G < N ? s0 + G : N;
+            bool any = false;
+            if (two)
+                for (size_t k = s0; k < s1; ++k) any = any || fluid(k);
+            for (size_t k = s0; k < s1; ++k)
+                if (any || fluid(k)) fn(k);
+        }
+    };
+    size_t len = 0;
+    visit([&](size_t) { ++len; });
+    if (len == 0 || (p.node_list == 0 && (two || 10 * len > 9 * N))) return 0;
+    if (out && mask) {
+        out->reserve(len);
+        visit([&](size_t k) { out->push_back(make_uint2((unsigned)k, (*mask)[k])); });
+    }
+    return len;
+}
+
 struct Plan3 {
-    size_t lat, off1, offm, total;
+    size_t lat, off1, offm, offl, total;
     bool has_mask;
 };
-Plan3 plan3(const lbm3_params &p, bool has_mask) {
+Plan3 plan3(const lbm3_params &p, bool has_mask, size_t nlist) {
     Plan3 pl;
     const size_t N = (size_t)p.nx * p.ny * p.nz;
     const size_t es = p.precision == LBM_F64 ? 8 : (p.precision == LBM_F32 ? 4 : 2);
@@ -567,7 +722,8 @@ Plan3 plan3(const lbm3_params &p, bool has_mask) {
     pl.off1 = p.pattern == LBM_AA ? 0 : al256(pl.lat); // AA: one lattice
     pl.offm = pl.off1 + al256(pl.lat);
     pl.has_mask = has_mask;
-    pl.total = pl.offm + (has_mask ? al256(N * 4) : 0);
+    pl.offl = pl.offm + (has_mask ? al256(N * 4) : 0);
+    pl.total = pl.offl + al256(nlist * sizeof(uint2));
     return pl;
 }
 bool any_bounce(const lbm3_params &p) {
@@ -620,7 +776,14 @@ template <class T> cudaError_t step3aa(lbm3_ctx *c) {
 #define LBM3_AA(HM, HF)                                                                    \
     (pp ? (k3_step_aa<T, HM, HF, true><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A), 0)    \
         : (k3_step_aa<T, HM, HF, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A), 0))
-    if (c->g.mask) {
+#define LBM3_AA_LIST(HF)                                                                    \
+    (pp ? (k3_step_aa_list<T, HF, true><<<gl, BLOCK3, 0, c->stream>>>(c->g, c->ph, A), 0)   \
+        : (k3_step_aa_list<T, HF, false><<<gl, BLOCK3, 0, c->stream>>>(c->g, c->ph, A), 0))
+    if (c->g.list) {
+        const dim3 gl((c->g.nlist + BLOCK3 - 1) / BLOCK3);
+        if (F) LBM3_AA_LIST(true);
+        else LBM3_AA_LIST(false);
+    } else if (c->g.mask) {
         if (F) LBM3_AA(true, true);
         else LBM3_AA(true, false);
     } else {
@@ -628,6 +791,7 @@ template <class T> cudaError_t step3aa(lbm3_ctx *c) {
         else LBM3_AA(false, false);
     }
 #undef LBM3_AA
+#undef LBM3_AA_LIST
     return cudaGetLastError();
 }
 template <class T> cudaError_t step3(lbm3_ctx *c) {
@@ -635,7 +799,11 @@ template <class T> cudaError_t step3(lbm3_ctx *c) {
     T *B = static_cast<T *>(c->lat[1 - c->cur]);
     const bool F = c->p.fx != 0.0 || c->p.fy != 0.0 || c->p.fz != 0.0;
     const dim3 gr = grid3(c->g);
-    if (c->g.mask) {
+    if (c->g.list) {
+        const dim3 gl((c->g.nlist + BLOCK3 - 1) / BLOCK3);
+        if (F) k3_step_list<T, true><<<gl, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
+        else k3_step_list<T, false><<<gl, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
+    } else if (c->g.mask) {
         if (F) k3_step<T, true, true><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
         else k3_step<T, true, false><<<gr, BLOCK3, 0, c->stream>>>(c->g, c->ph, A, B);
     } else {
@@ -658,7 +826,8 @@ extern "C" {
 
 lbm_status lbm3_workspace_bytes(const lbm3_params *p, size_t *bytes) {
     if (check3(p) || !bytes) return LBM_ERR_INVALID;
-    *bytes = plan3(*p, any_bounce(*p)).total;
+    const bool any = any_bounce(*p);
+    *bytes = plan3(*p, any, node_list3(*p, any, nullptr, nullptr)).total;
     return LBM_OK;
 }
 
@@ -670,7 +839,9 @@ lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lb
     std::vector<uint32_t> mask;
     bool any = false;
     const long long nf = build_mask3(*p, mask, any);
-    const Plan3 pl = plan3(*p, any);
+    std::vector<uint2> list;
+    const size_t nlist = node_list3(*p, any, &mask, &list);
+    const Plan3 pl = plan3(*p, any, nlist);
     if (bytes < pl.total) return LBM_ERR_OOM;
     lbm3_ctx *c = new lbm3_ctx();
     c->p = *p;
@@ -691,6 +862,10 @@ lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lb
     g.pz = p->periodic_z != 0;
     g.N = (unsigned long long)p->nx * p->ny * p->nz;
     g.mask = any ? reinterpret_cast<const uint32_t *>(ws + pl.offm) : nullptr;
+    g.list = nlist ? reinterpret_cast<const uint2 *>(ws + pl.offl) : nullptr;
+    g.nlist = (unsigned)nlist;
+    g.mx = 0xFFFFFFFFu / (unsigned)p->nx;
+    g.my = 0xFFFFFFFFu / (unsigned)p->ny;
     Phys3 &ph = c->ph;
     ph.om = 1.0 / p->tau;
     ph.kk = 1.0 - 0.5 * ph.om;
@@ -706,6 +881,10 @@ lbm_status lbm3_create(const lbm3_params *p, void *d_workspace, size_t bytes, lb
     if (!st && any)
         st = cuda3(c, cudaMemcpyAsync(ws + pl.offm, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice, c->stream),
                    "copy link mask");
+    if (!st && nlist)
+        st = cuda3(c, cudaMemcpyAsync(ws + pl.offl, list.data(), nlist * sizeof(uint2), cudaMemcpyHostToDevice,
+                                      c->stream),
+                   "copy node list");
     if (!st) st = cuda3(c, cudaStreamSynchronize(c->stream), "create sync");
     if (st) {
         delete c;
@@ -810,6 +989,8 @@ lbm_status lbm3_set_f(lbm3_ctx *ctx, const void *d_f) {
 }
 
 long long lbm3_fluid_nodes(const lbm3_ctx *ctx) { return ctx ? ctx->nfluid : -1; }
+
+long long lbm3_list_nodes(const lbm3_ctx *ctx) { return ctx ? (long long)ctx->g.nlist : -1; }
 long long lbm3_step_count(const lbm3_ctx *ctx) { return ctx ? ctx->steps : -1; }
 const char *lbm3_last_error(const lbm3_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
 

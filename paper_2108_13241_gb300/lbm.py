@@ -75,7 +75,11 @@ class lbm3_params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("pattern", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("node_list", ctypes.c_int),
     ]
+
+
+NODE_LISTS = {"auto": 0, "never": 1, "always": 2}
 
 
 _lib = None
@@ -132,6 +136,7 @@ def _load():
         "lbm3_get_f": ([_vp, _vp], st),
         "lbm3_set_f": ([_vp, _vp], st),
         "lbm3_fluid_nodes": ([_vp], ctypes.c_longlong),
+        "lbm3_list_nodes": ([_vp], ctypes.c_longlong),
         "lbm3_step_count": ([_vp], ctypes.c_longlong),
         "lbm3_last_error": ([_vp], ctypes.c_char_p),
     }
@@ -602,10 +607,14 @@ class LBM3:
     """One D3Q19 context (lbm3_* of include/lbm.h) on the current CUDA device
     and stream: dense, two lattices, stationary half-way bounce-back walls on
     the faces of non-periodic axes and on solid nodes, uniform Guo force.
-    Canonical arrays: f [19, nz, ny, nx], u [3, nz, ny, nx], rho [nz, ny, nx]."""
+    Canonical arrays: f [19, nz, ny, nx], u [3, nz, ny, nx], rho [nz, ny, nx].
+    node_list: "auto" (a node list for the AA pattern on sparse geometries),
+    "never" (the dense grid) or "always" (whenever a link bounces); FP64 /
+    FP32 only."""
 
     def __init__(self, nx: int, ny: int, nz: int, tau: float, solid=None, force=(0.0, 0.0, 0.0),
-                 periodic=(True, True, True), precision="f32", device="cuda", pattern="two_lattice"):
+                 periodic=(True, True, True), precision="f32", device="cuda", pattern="two_lattice",
+                 node_list="auto"):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         p = lbm3_params()
         p.nx, p.ny, p.nz = self.nx, self.ny, self.nz
@@ -621,6 +630,7 @@ class LBM3:
         p.precision = prec
         p.pattern = PATTERNS[pattern] if isinstance(pattern, str) else int(pattern)
         p.stream = torch.cuda.current_stream().cuda_stream or None
+        p.node_list = NODE_LISTS[node_list] if isinstance(node_list, str) else int(node_list)
         self.dtype = torch.float64 if prec == LBM_F64 else torch.float32
         self.device = torch.device(device)
         n = ctypes.c_size_t(0)
@@ -650,6 +660,11 @@ class LBM3:
     @property
     def fluid_nodes(self) -> int:
         return _load().lbm3_fluid_nodes(self.ctx)
+
+    @property
+    def list_nodes(self) -> int:
+        """Entries of the node list the step runs over (0: the dense grid)."""
+        return _load().lbm3_list_nodes(self.ctx)
 
     @property
     def steps(self) -> int:

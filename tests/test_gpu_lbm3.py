@@ -317,3 +317,77 @@ def test_porous_spheres_crop_matches_oracle(L, o3):
             if prec == "f64":
                 assert rel_l2(f, A, fl) <= 1e-12, pattern
             assert rel_l2(v.double().cpu().numpy(), u_ref, fl) <= 1e-5, (prec, pattern)
+
+
+def listed_count(solid, shape, precision, pattern):
+    """Entries the node list should hold: fluid nodes and, with two lattices,
+    the solid nodes sharing a 32-byte sector (4 FP64 / 8 FP32 nodes of
+    consecutive index) with a fluid node."""
+    n = int(np.prod(shape))
+    fl = np.ones(n, bool) if solid is None else ~np.asarray(solid, bool).reshape(-1)
+    if pattern == "aa":
+        return int(fl.sum())
+    g = 4 if precision == "f64" else 8
+    pad = np.zeros(-(-n // g) * g, bool)
+    pad[:n] = fl
+    any_fluid = np.repeat(pad.reshape(-1, g).any(1), g)[:n]
+    return int(any_fluid.sum())
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("pattern", ["two_lattice", "aa"])
+@pytest.mark.parametrize("name", ["porous_walls_force", "ragged_all_walls", "spheres_crop"])
+def test_node_list_equals_dense_grid(L, o3, name, pattern, precision):
+    """The listed step (one thread per listed node, coordinates from the
+    node index) gives the dense grid's state and macros bit for bit after
+    odd and even step counts, on ragged boxes and a crop of the porous
+    spheres; the list holds the fluid nodes and, with two lattices, the
+    solid nodes sharing a sector with them."""
+    if name == "spheres_crop":
+        solid_full, _ = inputs.porous_spheres_3d(256, 0.5)
+        solid = np.ascontiguousarray(solid_full[:40, :36, :44])
+        s = o3.Setup3(44, 36, 40, 0.8, periodic=(True, True, False), force=(1e-5, 2e-6, 0.0))
+        rho = 1.0 + 0.01 * inputs.random_field((40, 36, 44), 401)
+        u = 0.03 * inputs.random_field((3, 40, 36, 44), 402)
+    else:
+        s, solid, rho, u = setup(o3, name)
+    m, _ = o3.link_mask(s, solid)
+    fl = m != o3.SOLID
+    for steps in (5, 6):
+        out = {}
+        for mode in ("never", "always"):
+            sim = L.LBM3(s.nx, s.ny, s.nz, s.tau, solid=solid, force=s.force, periodic=s.periodic,
+                         precision=precision, pattern=pattern, node_list=mode)
+            if mode == "never":
+                assert sim.list_nodes == 0
+            else:
+                assert sim.list_nodes == listed_count(solid, (s.nz, s.ny, s.nx), precision, pattern)
+            sim.init_equilibrium(rho, u)
+            sim.step(steps)
+            r, v = sim.macros()
+            out[mode] = (sim.get_f().cpu().numpy(), r.cpu().numpy(), v.cpu().numpy())
+            sim.close()
+        fd, rd, ud = out["never"]
+        fs, rs, us = out["always"]
+        assert np.array_equal(fs[:, fl], fd[:, fl]), steps
+        assert np.array_equal(rs, rd) and np.array_equal(us, ud), steps
+
+
+def test_node_list_chosen_on_sparse_boxes_only(L):
+    """auto: a list for the AA pattern when it holds at most 90% of the
+    nodes (the porous spheres), the dense grid with two lattices and on a
+    box with walls only; FP16s storage always runs its dense pair kernel."""
+    solid_full, _ = inputs.porous_spheres_3d(256, 0.5)
+    solid = np.ascontiguousarray(solid_full[:32, :32, :32])
+    sim = L.LBM3(32, 32, 32, 0.8, solid=solid, precision="f32", pattern="aa")
+    assert 0 < sim.list_nodes < 0.9 * 32 ** 3
+    sim.close()
+    sim = L.LBM3(32, 32, 32, 0.8, solid=solid, precision="f32")
+    assert sim.list_nodes == 0
+    sim.close()
+    sim = L.LBM3(32, 32, 32, 0.8, periodic=(True, True, False), precision="f32", pattern="aa")
+    assert sim.list_nodes == 0
+    sim.close()
+    sim = L.LBM3(32, 32, 32, 0.8, solid=solid, precision="f16s", node_list="always")
+    assert sim.list_nodes == 0
+    sim.close()

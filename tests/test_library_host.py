@@ -190,3 +190,44 @@ def test_d3q19_invalid_parameters_rejected(lbm, bad):
     p, _ = _p3(lbm, kw["nx"], kw["ny"], kw["nz"], kw["precision"], tau=kw["tau"])
     st, _ = _ws3(lbm, p)
     assert st == lbm.LBM_ERR_INVALID
+
+
+def test_d3q19_workspace_holds_the_node_list(lbm):
+    """The node list (8 bytes an entry: node index, link mask) joins the
+    workspace with the AA pattern when it holds at most 90% of the nodes
+    (auto), always with node_list = 2, never with 1 or for FP16s; two
+    lattices list the solid nodes that share a 32-byte sector with a fluid
+    node (used with node_list = 2 only), AA only the fluid nodes."""
+    def al(b):
+        return (b + 255) // 256 * 256
+    nx, ny, nz = 24, 10, 8
+    N = nx * ny * nz
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[:, :, 3:20] = 1            # x = 0..2 and 20..23 fluid: 7 of 24 a row
+    fl = (solid.reshape(-1) == 0)
+    for prec, s, g in (("f64", 8, 4), ("f32", 4, 8)):
+        for pat, nl in (("two_lattice", 2), ("aa", 1)):
+            if pat == "aa":
+                n_list = int(fl.sum())
+            else:
+                n_list = int(np.repeat(fl.reshape(-1, g).any(1), g).sum())
+            base = nl * al(19 * N * s) + al(4 * N)
+            for mode, want in ((0, n_list if pat == "aa" else 0), (1, 0), (2, n_list)):
+                p, keep = _p3(lbm, nx, ny, nz, prec, pat, solid=solid)
+                p.node_list = mode
+                st, b = _ws3(lbm, p)
+                assert st == lbm.LBM_OK and b == base + al(8 * want), (prec, pat, mode)
+    # walls only: every node would be listed -- auto keeps the dense grid
+    p, _ = _p3(lbm, nx, ny, nz, "f32", periodic=(1, 0, 1))
+    st, b = _ws3(lbm, p)
+    assert st == lbm.LBM_OK and b == 2 * al(19 * N * 4) + al(4 * N)
+    p.node_list = 2
+    st, b = _ws3(lbm, p)
+    assert st == lbm.LBM_OK and b == 2 * al(19 * N * 4) + al(4 * N) + al(8 * N)
+    # FP16s runs its dense pair kernel
+    p, keep = _p3(lbm, nx, ny, nz, "f16s", solid=solid)
+    p.node_list = 2
+    st, b = _ws3(lbm, p)
+    assert st == lbm.LBM_OK and b == 2 * al(19 * N * 2) + al(4 * N)
+    p.node_list = 3
+    assert _ws3(lbm, p)[0] == lbm.LBM_ERR_INVALID
