@@ -686,7 +686,8 @@ def d3q19_rows(peak: float, stream, n: int = 256, steps: int = 200):
     (U 0.05, tau 0.8), FP64, FP32 and FP16-shifted storage, `steps` timed
     steps after 10 warm-up ones: GLUPS, the fraction of the 2 x 19 x s bytes
     per node (304 / 152 / 76 B) at the measured HBM peak, and the relative L2
-    error of u against the FP64 run after the same steps."""
+    error of u against the FP64 run after the same steps; FP32 AA on the same
+    box; FP32 on an n^3 porous medium of random spheres (porosity 0.5)."""
     import torch
     from paper_2108_13241_gb300 import inputs, lbm
     rho, u = inputs.taylor_green_3d(n, n, n, 0.05)
@@ -996,8 +997,9 @@ def main():
     ap.add_argument("--adjoint", action="store_true",
                     help="run the adjoint cost on the 512 x 256 channel and on a 2048 x 2048 one")
     ap.add_argument("--d3q19", action="store_true",
-                    help="run the D3Q19 step on an n^3 3-D Taylor-Green box (n = --n, default 256 here, "
-                         "plus a 1024^3 box from rest unless --n is given)")
+                    help="run the D3Q19 step on an n^3 3-D Taylor-Green box and an n^3 porous medium of "
+                         "spheres (n = --n, default 256 here), plus a 1024^3 two-lattice and a 1280^3 AA box "
+                         "from rest unless --n is given")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.d3q19:
