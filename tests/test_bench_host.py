@@ -42,3 +42,16 @@ def test_sector_nodes_by_brute_force():
                 if (solid[y, x0:x0 + seg] == 0).any():
                     want += seg
         assert bench.sector_nodes(solid, prec) == want
+
+
+def test_sector_nodes_of_a_box_by_brute_force():
+    """The 3-D rows count sectors on the box's rows (z, y) stacked along x."""
+    rng = np.random.default_rng(6)
+    solid = (rng.random((5, 7, 64)) < 0.6).astype(np.uint8)
+    want = 0
+    for z in range(5):
+        for y in range(7):
+            for x0 in range(0, 64, 8):
+                if (solid[z, y, x0:x0 + 8] == 0).any():
+                    want += 8
+    assert bench.sector_nodes(solid.reshape(-1, 64), "f32") == want
