@@ -615,6 +615,8 @@ class LBM3:
     def __init__(self, nx: int, ny: int, nz: int, tau: float, solid=None, force=(0.0, 0.0, 0.0),
                  periodic=(True, True, True), precision="f32", device="cuda", pattern="two_lattice",
                  node_list="auto"):
+        if isinstance(node_list, str) and node_list not in NODE_LISTS:
+            raise ValueError("node_list must be one of %s" % sorted(NODE_LISTS))
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         p = lbm3_params()
         p.nx, p.ny, p.nz = self.nx, self.ny, self.nz

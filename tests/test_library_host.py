@@ -231,3 +231,8 @@ def test_d3q19_workspace_holds_the_node_list(lbm):
     assert st == lbm.LBM_OK and b == 2 * al(19 * N * 2) + al(4 * N)
     p.node_list = 3
     assert _ws3(lbm, p)[0] == lbm.LBM_ERR_INVALID
+
+
+def test_d3q19_binding_rejects_unknown_node_list_mode(lbm):
+    with pytest.raises(ValueError):
+        lbm.LBM3(8, 8, 8, 0.8, node_list="sometimes")
