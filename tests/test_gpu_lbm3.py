@@ -190,6 +190,38 @@ def test_benchmark_box_one_step_matches_oracle(L, o3):
     assert rel_l2(v, u_ref, fl) <= 1e-5
 
 
+@pytest.mark.parametrize("pattern", ["two_lattice", "aa"])
+def test_porous_spheres_benchmark_box_one_step_matches_oracle(L, o3, pattern):
+    """The benchmark's porous configuration (256^3 random spheres, porosity
+    0.5, force along x, FP32; two lattices on the dense grid, AA over the
+    node list -- the launches bench.py times): one step from the GPU's own
+    state after 10 steps from a Taylor-Green velocity field, against the
+    oracle's step from that state (FP32 storage rounding only: 1e-6
+    relative L2 on f, 1e-5 on u, fluid nodes)."""
+    n = 256
+    solid, _ = inputs.porous_spheres_3d(n, 0.5)
+    rho, u = inputs.taylor_green_3d(n, n, n, 0.05)
+    sim = L.LBM3(n, n, n, 0.8, solid=solid, force=(1e-6, 0.0, 0.0), precision="f32", pattern=pattern)
+    assert (sim.list_nodes > 0) == (pattern == "aa")
+    sim.init_equilibrium(rho, u)
+    del rho, u
+    sim.step(10)
+    A = sim.get_f().double().cpu().numpy()
+    sim.step(1)
+    f = sim.get_f().double().cpu().numpy()
+    _, v = sim.macros()
+    v = v.double().cpu().numpy()
+    sim.close()
+    s = o3.Setup3(n, n, n, 0.8, force=(1e-6, 0.0, 0.0))
+    m, _ = o3.link_mask(s, solid)
+    B = o3.step(s, m, A)
+    del A
+    _, u_ref = o3.macros(s, m, B)
+    fl = m != o3.SOLID
+    assert rel_l2(f, B, fl) <= 1e-6
+    assert rel_l2(v, u_ref, fl) <= 1e-5
+
+
 def test_box_beyond_32_bit_slot_offsets_equals_its_tiled_period(L):
     """640^3 nodes (19 x 640^3 > 2^32 values a lattice: 64-bit slot offsets,
     40 GB of FP32 lattices): a 3-D Taylor-Green field of period 64 tiled ten
