@@ -13,6 +13,8 @@
 // regrouped per pair of opposite links into an even part and an odd part
 // (exact algebra, fewer operations).  The register footprint stays small
 // (19 values a thread), the concern the paper raises for three dimensions.
+// On sparse geometries a node list (index and link mask per entry) lets the
+// step run one thread per fluid node instead of one per grid node.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -300,7 +302,9 @@ __device__ __forceinline__ void collide3(T f[Q3], T om, T kk, T Fx, T Fy, T Fz) 
 }
 
 // Whether a solid node shares its 32-byte DRAM sector with a fluid node of
-// its warp (lanes in aligned groups of 32 / bytes-per-lane): such a node
+// its warp (lanes in aligned groups of 32 / bytes-per-lane, which match the
+// sectors when n_x is a multiple of the group; otherwise some writes stay
+// partial, which costs time, not correctness): such a node
 // writes zeros -- what every solid node holds, and never read -- so that the
 // sector is stored whole and the memory does not first read the old sector
 // to merge a partial write (the two-lattice step writes a lattice it has not
